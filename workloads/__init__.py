@@ -1,0 +1,212 @@
+"""Seeded synthetic inputs for the block-layer SR step.
+
+This module is shared by the CUDA path, the oracle, the tests and the bench.
+It holds no arithmetic of the method itself: it only draws random numbers,
+builds lattice bond lists (geometry) and names the five workload shapes.
+
+Conventions (each one a reading of the paper where it is silent):
+
+* Spin configurations x in {-1,+1}^N with zero total S^z: every row is an
+  independent random permutation of N/2 up-spins and N/2 down-spins
+  (duplicates allowed), drawn with ``numpy.random.default_rng(seed)``.
+* Lattices are periodic (Sec. 3, Heisenberg chain and J1-J2 paragraphs).
+  Site index r = y*L + x. Chain bonds (i, i+1 mod N). Square lattice: for
+  each site in order its J1 bonds (right, down), then after all J1 bonds,
+  for each site its J2 bonds (down-right, down-left). This fixes the bond
+  order, and with it the order of connected configurations.
+* Parameters are complex. RBM layout: [a (N) | b (M) | W (M x N, row-major)].
+  FFNN layout: per layer l, [W_l (out x in, row-major) | b_l (out)]; hidden
+  layers use ln cosh, the last layer is linear with one output. Each layer
+  is one block of the block-layer QGT (Sec. 2, Eq. 3: one block per module).
+* Initial weights: real and imaginary parts drawn independently, all real
+  parts first then all imaginary parts, in flat parameter order. RBM std
+  0.01 per part; FFNN std sqrt(1/(2 fan_in)) per part (so E|w|^2 = 1/fan_in).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+RBM = 0
+FFNN = 1
+
+
+@dataclasses.dataclass
+class Model:
+    """A complex NQS architecture (no parameter values)."""
+    kind: int                      # RBM or FFNN
+    widths: Tuple[int, ...]        # FFNN: (N, h1, ..., 1); RBM: (N, M)
+
+    @property
+    def n_sites(self) -> int:
+        return self.widths[0]
+
+    def layer_shapes(self) -> List[Tuple[int, int]]:
+        """(out, in) for each FFNN layer."""
+        assert self.kind == FFNN
+        return [(self.widths[i + 1], self.widths[i]) for i in range(len(self.widths) - 1)]
+
+    def block_sizes(self) -> List[int]:
+        if self.kind == RBM:
+            n, m = self.widths
+            return [n, m, m * n]
+        return [o * i + o for (o, i) in self.layer_shapes()]
+
+    def block_offsets(self) -> np.ndarray:
+        sz = self.block_sizes()
+        off = np.zeros(len(sz) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(sz)
+        return off
+
+    @property
+    def n_params(self) -> int:
+        return int(sum(self.block_sizes()))
+
+    def init_std(self) -> np.ndarray:
+        """Per-parameter std of each of the real and imaginary parts."""
+        if self.kind == RBM:
+            return np.full(self.n_params, 0.01)
+        parts = []
+        for (o, i) in self.layer_shapes():
+            s = math.sqrt(1.0 / (2.0 * i))
+            parts.append(np.full(o * i + o, s))
+        return np.concatenate(parts)
+
+
+def init_params(model: Model, rng: np.random.Generator) -> np.ndarray:
+    """complex128 flat parameter vector, drawn from ``rng``."""
+    std = model.init_std()
+    re = rng.standard_normal(model.n_params)
+    im = rng.standard_normal(model.n_params)
+    return (re * std + 1j * (im * std)).astype(np.complex128)
+
+
+def zero_sz_configs(n_sites: int, n_samples: int, rng: np.random.Generator) -> np.ndarray:
+    """int8 [n_samples, n_sites], each row a permutation with zero total S^z."""
+    if n_sites % 2:
+        raise ValueError("zero total S^z needs an even number of sites")
+    base = np.array([1] * (n_sites // 2) + [-1] * (n_sites // 2), dtype=np.int8)
+    out = np.empty((n_samples, n_sites), dtype=np.int8)
+    for s in range(n_samples):
+        out[s] = rng.permutation(base)
+    return out
+
+
+def chain_bonds(n: int, j: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
+    """Periodic chain: bonds (i, i+1 mod n). Returns (int32 [nb,2], float64 [nb])."""
+    if n < 3:
+        raise ValueError("periodic chain needs n >= 3")
+    ij = np.array([[i, (i + 1) % n] for i in range(n)], dtype=np.int32)
+    return ij, np.full(n, float(j))
+
+
+def square_j1j2_bonds(lx: int, ly: Optional[int] = None, j1: float = 1.0,
+                      j2: float = 0.5) -> Tuple[np.ndarray, np.ndarray]:
+    """Periodic lx x ly square lattice, J1 list then J2 list (site-major)."""
+    ly = lx if ly is None else ly
+    if lx < 3 or ly < 3:
+        raise ValueError("periodic square lattice needs sides >= 3")
+    site = lambda x, y: (y % ly) * lx + (x % lx)
+    b1, b2 = [], []
+    for y in range(ly):
+        for x in range(lx):
+            b1.append((site(x, y), site(x + 1, y)))
+            b1.append((site(x, y), site(x, y + 1)))
+    for y in range(ly):
+        for x in range(lx):
+            b2.append((site(x, y), site(x + 1, y + 1)))
+            b2.append((site(x, y), site(x - 1, y + 1)))
+    ij = np.array(b1 + b2, dtype=np.int32)
+    jj = np.array([j1] * len(b1) + [j2] * len(b2), dtype=np.float64)
+    return ij, jj
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    model: Model
+    theta: np.ndarray              # complex128 [n_p]
+    configs: np.ndarray            # int8 [n_s, N]
+    bond_ij: np.ndarray            # int32 [nb, 2]
+    bond_j: np.ndarray             # float64 [nb]
+    block_off: np.ndarray          # int64 [n_blocks+1]
+    diag_shift: float
+    cutoff: float
+    precision: str                 # "fp64" | "fp32" | "split_bf16"
+    c: float = 1.0                 # spin units: 1 = Pauli (sigma.sigma)
+    sign_rule: int = 1             # +1: no Marshall sign; -1: Marshall sign
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.configs.shape[0])
+
+
+def _ffnn(n: int, hidden: Sequence[int]) -> Model:
+    return Model(FFNN, (n,) + tuple(hidden) + (1,))
+
+
+def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
+    """The five workload shapes of the benchmark, optionally with fewer samples.
+
+    * ``chain10_rbm``      RBM alpha=1 on a 10-site Heisenberg chain, 512 samples, FP64.
+    * ``j1j2_6x6_ffnn``    FFNN 36-64-64-1, 6x6 J1-J2 (J2=0.5), 4096 samples, FP32.
+    * ``j1j2_10x10_ffnn5`` FFNN 100-64-64-64-64-1, 10x10 J1-J2, 16384 samples, BF16 split.
+    * ``j1j2_10x10_ffnn256`` FFNN 100-256-256-1, 10x10 J1-J2, 32768 samples.
+    * ``batch8x8_<i>``     instance i (0..15) of the batched 8x8 workload.
+    """
+    if name == "chain10_rbm":
+        model = Model(RBM, (10, 10))
+        theta = init_params(model, np.random.default_rng(0))
+        ns = 512 if n_samples is None else n_samples
+        configs = zero_sz_configs(10, ns, np.random.default_rng(1))
+        ij, jj = chain_bonds(10, 1.0)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-4, 1e-10, "fp64")
+    if name == "j1j2_6x6_ffnn":
+        model = _ffnn(36, [64, 64])
+        theta = init_params(model, np.random.default_rng(2))
+        ns = 4096 if n_samples is None else n_samples
+        configs = zero_sz_configs(36, ns, np.random.default_rng(3))
+        ij, jj = square_j1j2_bonds(6, 6, 1.0, 0.5)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "fp32")
+    if name == "j1j2_10x10_ffnn5":
+        model = _ffnn(100, [64, 64, 64, 64])
+        rng = np.random.default_rng(4)
+        theta = init_params(model, rng)
+        ns = 16384 if n_samples is None else n_samples
+        configs = zero_sz_configs(100, ns, rng)
+        ij, jj = square_j1j2_bonds(10, 10, 1.0, 0.5)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "split_bf16")
+    if name == "j1j2_10x10_ffnn256":
+        model = _ffnn(100, [256, 256])
+        rng = np.random.default_rng(5)
+        theta = init_params(model, rng)
+        ns = 32768 if n_samples is None else n_samples
+        configs = zero_sz_configs(100, ns, rng)
+        ij, jj = square_j1j2_bonds(10, 10, 1.0, 0.5)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "split_bf16")
+    if name.startswith("batch8x8_"):
+        i = int(name.split("_")[1])
+        if not 0 <= i < 16:
+            raise ValueError(name)
+        cyc = [32, 64, 128]
+        hidden = [cyc[k % 3] for k in range(11)]
+        model = _ffnn(64, hidden)
+        rng = np.random.default_rng(10 + i)
+        theta = init_params(model, rng)
+        ns_i = 64 * int(round((2048 + 6144 * i / 15) / 64))
+        ns = ns_i if n_samples is None else n_samples
+        configs = zero_sz_configs(64, ns, rng)
+        ij, jj = square_j1j2_bonds(8, 8, 1.0, 0.6 * i / 15)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "split_bf16")
+    raise KeyError(name)
+
+
+WORKLOADS = ("chain10_rbm", "j1j2_6x6_ffnn", "j1j2_10x10_ffnn5", "j1j2_10x10_ffnn256")
