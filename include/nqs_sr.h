@@ -1,0 +1,226 @@
+/*
+ * nqs_sr.h -- C ABI of the block-layer stochastic-reconfiguration (SR) step
+ * for complex neural quantum states, hand-written CUDA for sm_103a (GB300).
+ *
+ * The step (Sec. 2 of "When Less is More: Approximating the Quantum Geometric
+ * Tensor with Block Structures", arXiv 2510.08430):
+ *   O_{s,k}  = d ln psi(x_s) / d theta_k                (definition below Eq. 2)
+ *   E_loc(x) = <x|H|psi> / <x|psi>                       (Eq. 1)
+ *   dO = O - <O>,  e = E_loc - <E>                        (second form of Eq. 2)
+ *   F_k = <conj(dO_k) e>                                  (Sec. 2: F = energy gradient)
+ *   S_b = <dO_b^H dO_b>  for each layer block b            (Eq. 3)
+ *   dtheta_b = -eta * pinv(S_b + lambda I) F_b             (Sec. 2, block-layer paragraph)
+ * Expectations <f> = sum_s w_s f(x_s), with w_s = 1/n_s unless weights are given.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * - Complex numbers are interleaved (re, im). "c128" = two doubles, "c64" = two floats.
+ * - Unless stated otherwise a pointer argument is a DEVICE pointer owned by the
+ *   caller; the library never frees or retains it after the call returns.
+ * - The library allocates no device memory. Scratch comes from a caller-provided
+ *   workspace (nqs_workspace_create), sized by the *_workspace_size queries.
+ * - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *   is the legacy default stream) and returns an int status. Host-side argument
+ *   errors and launch failures are returned directly. Device-detected errors
+ *   (non-finite values, sweep limits, wait budgets) are recorded in the
+ *   workspace and returned by nqs_sync_status, which synchronises `stream`.
+ * - No C++ exception, abort or device trap crosses this boundary.
+ * - Thread safety: distinct workspaces may be used concurrently from different
+ *   host threads; one workspace must not be used by overlapping calls.
+ */
+#ifndef NQS_SR_H
+#define NQS_SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NQS_API __attribute__((visibility("default")))
+#else
+#define NQS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define NQS_OK                 0
+#define NQS_ERR_INVALID_ARG   (-1) /* bad sizes, offsets, dtype/precision combination, NULL */
+#define NQS_ERR_CUDA          (-2) /* a CUDA runtime call or kernel launch failed */
+#define NQS_ERR_WORKSPACE     (-3) /* workspace too small; nqs_last_error states the size */
+#define NQS_ERR_NOT_CONVERGED (-4) /* an iterative eigen-solver step hit its sweep limit */
+#define NQS_ERR_TIMEOUT       (-5) /* a device-side wait exhausted its iteration budget */
+#define NQS_ERR_NONFINITE     (-6) /* NaN/Inf found in O, E_loc, S or the solve */
+#define NQS_ERR_UNSUPPORTED   (-7) /* valid request this build does not implement */
+
+/* ---- precision of the sample-space contractions (Jacobian, E_loc, Gram) ----
+ * NQS_FP64       : everything in FP64; O is c128.
+ * NQS_FP32       : Jacobian and E_loc in FP32 (O is c64), centring and force
+ *                  accumulated in FP64, Gram in FP32 FFMA.
+ * NQS_SPLIT_BF16 : as NQS_FP32, but the Gram runs on tcgen05 tensor cores with
+ *                  each centred entry split into BF16 hi + lo and three products
+ *                  (hi*hi + hi*lo + lo*hi) accumulated in FP32.
+ * NQS_SPLIT_BF16X3: three-way split hi + mid + lo and six products (all terms of
+ *                  order below 2^-16 relative), for a Gram accurate to ~FP32.
+ * In both split modes FP32 accumulation runs over chunks of 1024 samples whose
+ * partial Grams are summed in FP64.
+ * The per-block shifted eigen-decomposition and solve is FP64 in every mode. */
+typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3 } nqs_precision;
+
+enum { NQS_RBM = 0, NQS_FFNN = 1 };
+
+/* Network description (host struct; host pointer `widths`).
+ * RBM : widths = {N, M}; ln psi = sum_i a_i x_i + sum_j lncosh(b_j + sum_i W_ji x_i);
+ *       parameter layout [a (N) | b (M) | W (M x N row-major)]; 3 blocks.
+ * FFNN: widths = {N, h_1, ..., h_{L-1}, 1}; hidden layers z = W h + b, h' = lncosh(z),
+ *       last layer linear; layout per layer [W_l (out x in row-major) | b_l]; one
+ *       block per layer (Eq. 3: one block per module).
+ * lncosh(z) = s z - ln 2 + log1p(exp(-2 s z)), s = sign(Re z) (s = +1 at Re z = 0).
+ * Limits of this build: N <= 1024, every width <= 512, n_layers <= 32. */
+typedef struct {
+    int32_t kind;           /* NQS_RBM or NQS_FFNN */
+    int32_t n_layers;       /* number of weight layers (RBM: 1) = len(widths) - 1 */
+    const int32_t* widths;  /* HOST array of n_layers + 1 entries */
+} nqs_model;
+
+/* Spin Hamiltonian H = c * sum_b J_b (sx_i sx_j + sy_i sy_j + sz_i sz_j) over a bond
+ * list (Sec. 3: Heisenberg chain; J1-J2 square lattice). c = 1 is the Pauli
+ * normalisation of the energies in Table 2; c = 0.25 is S = sigma/2.
+ * sign_rule = -1 multiplies the off-diagonal (exchange) elements by -1.
+ * Bonds must have i != j and 0 <= i, j < n_sites. */
+typedef struct {
+    int32_t n_sites;
+    int32_t n_bonds;
+    const int32_t* bond_ij; /* DEVICE int32 [n_bonds][2] */
+    const double* bond_J;   /* DEVICE float64 [n_bonds] */
+    double c;
+    int32_t sign_rule;      /* +1 or -1 */
+} nqs_hamiltonian;
+
+/* ---- workspace (caller-owned device memory wrapped in a host handle) ---- */
+typedef struct nqs_workspace nqs_workspace;
+
+/* Wraps `bytes` of caller-allocated device memory starting at `device_ptr`
+ * (256-byte aligned). Allocates only the small host-side handle. */
+NQS_API int nqs_workspace_create(void* device_ptr, size_t bytes, nqs_workspace** ws);
+NQS_API int nqs_workspace_destroy(nqs_workspace* ws);
+
+/* Synchronises `stream`, returns the first device-detected status recorded in
+ * `ws` since the last call (NQS_OK if none) and clears it. */
+NQS_API int nqs_sync_status(nqs_workspace* ws, void* stream);
+
+/* Thread-local text of the last error (never NULL). */
+NQS_API const char* nqs_last_error(void);
+
+/* ---- workspace sizes ---- */
+NQS_API int nqs_jacobian_workspace_size(const nqs_model* m, int64_t n_s, int32_t precision, size_t* bytes);
+NQS_API int nqs_local_energy_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonian* h,
+                                    int32_t precision, size_t* bytes);
+NQS_API int qgt_block_build_workspace_size(int64_t n_s, int64_t n_p, const int64_t* block_off,
+                                   int32_t n_blocks, int32_t precision, size_t* bytes);
+NQS_API int qgt_block_solve_workspace_size(const int64_t* block_off, int32_t n_blocks, size_t* bytes);
+NQS_API int sr_step_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonian* h,
+                           const int64_t* block_off, int32_t n_blocks, int32_t precision,
+                           size_t* bytes);
+
+/* ---- packed block storage of S ----
+ * Block b (n_b = block_off[b+1] - block_off[b]) occupies n_b*n_b c128 elements
+ * starting at element sum_{b'<b} n_{b'}^2, row-major, S_b[k][l] at k*n_b + l.
+ * Only the lower triangle k >= l is defined; the rest is unspecified. */
+NQS_API int64_t qgt_packed_size(const int64_t* block_off, int32_t n_blocks); /* elements */
+
+/* nqs_jacobian -- ln psi and the log-derivative Jacobian (definition below Eq. 2).
+ *   theta      : c128 [n_p] parameters (layout of nqs_model).
+ *   configs    : int8 [n_s][N], entries +1 / -1, row-major.
+ *   logpsi_out : c128 [n_s].
+ *   O_out      : PARAMETER-MAJOR Jacobian, O_out[k*ldo + s] = d ln psi(x_s)/d theta_k;
+ *                c128 for NQS_FP64, c64 otherwise. ldo >= n_s. Columns n_s..ldo-1
+ *                of every row are written with zeros.
+ * The derivative is the complex (holomorphic) derivative; no conjugation. */
+NQS_API int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
+                 int32_t precision, void* logpsi_out, void* O_out, int64_t ldo,
+                 nqs_workspace* ws, void* stream);
+
+/* nqs_local_energy -- E_loc(x_s) (Eq. 1) for the Hamiltonian h:
+ *   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign_rule psi(x^{ij})/psi(x) ],
+ * x^{ij} = x with spins i and j flipped; connected configurations are visited in
+ * bond order. eloc_out: c128 [n_s]. Arithmetic in FP64 for NQS_FP64, else FP32. */
+NQS_API int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
+                     const nqs_hamiltonian* h, int32_t precision, void* eloc_out,
+                     nqs_workspace* ws, void* stream);
+
+/* nqs_connections -- the integer work of E_loc: for every sample, the bonds with
+ * x_i != x_j in bond order. conn_count: int32 [n_s]; conn_offset: int64 [n_s+1]
+ * (exclusive prefix sum); conn_bond: int32 [max_conn] receives the bond indices
+ * sample-major. *n_conn_out (host) receives the total; it is an error
+ * (NQS_ERR_INVALID_ARG) if max_conn is too small. Synchronises `stream`. */
+NQS_API int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h,
+                    int32_t* conn_count, int64_t* conn_offset, int32_t* conn_bond,
+                    int64_t max_conn, int64_t* n_conn_out, nqs_workspace* ws, void* stream);
+
+/* qgt_block_build -- means, centring, force and the block-layer QGT (Eq. 2, Eq. 3).
+ *   O        : parameter-major Jacobian as written by nqs_jacobian (c128 for NQS_FP64,
+ *              c64 otherwise), leading dimension ldo. OVERWRITTEN with the centred dO
+ *              for NQS_FP64/NQS_FP32; left unchanged in the split modes.
+ *   w        : float64 [n_s] sample weights summing to 1, or NULL for 1/n_s.
+ *   block_off: HOST int64 [n_blocks+1], block_off[0] = 0, strictly increasing,
+ *              block_off[n_blocks] = n_p.
+ *   eloc     : c128 [n_s].
+ *   S_packed : c128, qgt_packed_size elements (lower triangles, see above).
+ *   F_out    : c128 [n_p], F_k = sum_s w_s conj(dO_sk) e_s.
+ *   Omean_out: c128 [n_p] or NULL.   Emean_out: c128 [1] or NULL. */
+NQS_API int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const double* w,
+                    const int64_t* block_off, int32_t n_blocks, const void* eloc,
+                    int32_t precision, void* S_packed, void* F_out, void* Omean_out,
+                    void* Emean_out, nqs_workspace* ws, void* stream);
+
+/* qgt_block_solve -- per-block shifted pseudo-inverse solve (Sec. 2):
+ *   S~_b = S_b + diag_shift I = U diag(sigma) U^H (FP64),
+ *   keep_i = sigma_i > cutoff * max_i sigma_i   (cutoff_mode 0, relative)
+ *          = sigma_i > cutoff                   (cutoff_mode 1, absolute),
+ *   dtheta_b = -eta U diag(keep / sigma) U^H F_b.
+ * The eigen-decomposition is kept factored: S~_b = Q (T + diag_shift I) Q^H by
+ * Householder reduction (Q stored as reflectors in S_packed, which is
+ * OVERWRITTEN), and T = Z diag(sigma) Z^T; Z is formed only when some sigma_i
+ * is dropped. The result equals the definition up to rounding.
+ *   F         : c128 [n_p].             dtheta_out: c128 [n_p].
+ *   evals_out : float64 [n_p] or NULL; block b's sigma ascending at block_off[b].
+ *   n_kept_out: int32 [n_blocks] or NULL. */
+NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, const void* F,
+                    double diag_shift, double cutoff, int32_t cutoff_mode, double eta,
+                    void* dtheta_out, double* evals_out, int32_t* n_kept_out,
+                    nqs_workspace* ws, void* stream);
+
+/* sr_step -- one whole block-layer SR step: Jacobian, E_loc, centring, force,
+ * block Gram and the per-block solve, from (theta, configs) to dtheta and <E>.
+ *   dtheta_out: c128 [n_p]; Emean_out: c128 [1].
+ *   evals_out / n_kept_out as in qgt_block_solve (may be NULL).
+ *   flags: NQS_SYNC makes the call synchronise and return device status. */
+#define NQS_SYNC 1
+NQS_API int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
+            const nqs_hamiltonian* h, const int64_t* block_off, int32_t n_blocks,
+            double diag_shift, double cutoff, int32_t cutoff_mode, double eta,
+            int32_t precision, void* dtheta_out, void* Emean_out, double* evals_out,
+            int32_t* n_kept_out, int32_t flags, nqs_workspace* ws, void* stream);
+
+/* ---- measurement hooks ----
+ * nqs_stage_timing(ws, 1) makes later sr_step calls on `ws` record CUDA events
+ * on their stream at the stage boundaries: [0] Jacobian (parameter conversion,
+ * forward, backward, O write), [1] local energies, [2] means/centring/force,
+ * [3] block Gram, [4] Householder tridiagonal reduction, [5] eigenvalues, solve
+ * and back-transform. nqs_stage_times synchronises on the last event and
+ * returns the milliseconds of each stage of the most recent timed sr_step.
+ * nqs_launch_count returns the number of kernels this library has launched in
+ * the process (all threads). */
+NQS_API int nqs_stage_timing(nqs_workspace* ws, int32_t enable);
+NQS_API int nqs_stage_times(nqs_workspace* ws, double* ms_out, int32_t max_stages, int32_t* n_stages);
+NQS_API int64_t nqs_launch_count(void);
+
+/* Library version string. */
+NQS_API const char* nqs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_SR_H */

@@ -1,0 +1,272 @@
+"""Python binding of the nqs_sr C ABI: argument marshalling only.
+
+Each function has the name of the C entry point it calls. Tensors are torch
+CUDA tensors (PyTorch supplies device memory and the current stream); every
+stage of the computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SYNC, check,
+                   nqs_hamiltonian, nqs_model)
+
+PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3}
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> C.c_void_p:
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Model:
+    """Network description: kind (0 RBM, 1 FFNN) and widths."""
+
+    def __init__(self, kind: int, widths: Sequence[int]):
+        self.kind = int(kind)
+        self.widths = [int(w) for w in widths]
+        self._w = (C.c_int32 * len(self.widths))(*self.widths)
+        self.c = nqs_model(self.kind, len(self.widths) - 1, self._w)
+
+    @classmethod
+    def from_workload(cls, m) -> "Model":
+        return cls(m.kind, m.widths)
+
+    def block_offsets(self) -> np.ndarray:
+        if self.kind == NQS_RBM:
+            n, m = self.widths
+            sz = [n, m, m * n]
+        else:
+            sz = [self.widths[i + 1] * self.widths[i] + self.widths[i + 1] for i in range(len(self.widths) - 1)]
+        return np.concatenate([[0], np.cumsum(sz)]).astype(np.int64)
+
+
+class Hamiltonian:
+    """Bond Hamiltonian; bond arrays are copied to the device."""
+
+    def __init__(self, n_sites: int, bond_ij, bond_j, c: float = 1.0, sign_rule: int = 1, device="cuda"):
+        self.bond_ij = torch.as_tensor(np.ascontiguousarray(bond_ij, dtype=np.int32), device=device)
+        self.bond_j = torch.as_tensor(np.ascontiguousarray(bond_j, dtype=np.float64), device=device)
+        self.c = nqs_hamiltonian(int(n_sites), int(self.bond_ij.shape[0]), self.bond_ij.data_ptr(),
+                                 self.bond_j.data_ptr(), float(c), int(sign_rule))
+
+
+class Workspace:
+    """Caller-owned device scratch (a torch uint8 tensor) wrapped in a library handle."""
+
+    def __init__(self, nbytes: int = 0, device="cuda"):
+        self.device = device
+        self.buf = None
+        self.h = C.c_void_p(0)
+        self.nbytes = 0
+        if nbytes:
+            self.ensure(nbytes)
+
+    def ensure(self, nbytes: int) -> "Workspace":
+        if nbytes <= self.nbytes:
+            return self
+        lib = _lib.load()
+        if self.h.value:
+            lib.nqs_workspace_destroy(self.h)
+        self.buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+        base = (self.buf.data_ptr() + 255) // 256 * 256
+        self.h = C.c_void_p(0)
+        check(lib.nqs_workspace_create(C.c_void_p(base), C.c_size_t(int(nbytes)), C.byref(self.h)))
+        self.nbytes = int(nbytes)
+        return self
+
+    def sync_status(self) -> None:
+        check(_lib.load().nqs_sync_status(self.h, _stream()))
+
+    def __del__(self):
+        try:
+            if self.h.value:
+                _lib.load().nqs_workspace_destroy(self.h)
+        except Exception:
+            pass
+
+
+def _size(fn, *args) -> int:
+    out = C.c_size_t(0)
+    check(fn(*args, C.byref(out)))
+    return out.value
+
+
+def _off(block_off) -> C.Array:
+    arr = np.ascontiguousarray(block_off, dtype=np.int64)
+    return (C.c_int64 * len(arr))(*arr.tolist())
+
+
+def _cdt(precision: int):
+    return torch.complex128 if precision == NQS_FP64 else torch.complex64
+
+
+def nqs_jacobian(model: Model, theta: torch.Tensor, configs: torch.Tensor, precision="fp64",
+                 ldo: Optional[int] = None, ws: Optional[Workspace] = None, sync: bool = True):
+    """(logpsi c128 [n_s], O parameter-major [n_p, ldo] c128/c64)."""
+    lib = _lib.load()
+    p = _prec(precision)
+    ns = int(configs.shape[0])
+    ldo = ns if ldo is None else int(ldo)
+    n_p = int(model.block_offsets()[-1])
+    ws = ws or Workspace()
+    ws.ensure(_size(lib.nqs_jacobian_workspace_size, C.byref(model.c), ns, p))
+    logpsi = torch.empty(ns, dtype=torch.complex128, device=configs.device)
+    O = torch.empty((n_p, ldo), dtype=_cdt(p), device=configs.device)
+    check(lib.nqs_jacobian(C.byref(model.c), _ptr(theta), _ptr(configs), ns, p, _ptr(logpsi), _ptr(O), ldo,
+                           ws.h, _stream()))
+    if sync:
+        ws.sync_status()
+    return logpsi, O
+
+
+def nqs_local_energy(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian,
+                     precision="fp64", ws: Optional[Workspace] = None, sync: bool = True) -> torch.Tensor:
+    lib = _lib.load()
+    p = _prec(precision)
+    ns = int(configs.shape[0])
+    ws = ws or Workspace()
+    ws.ensure(_size(lib.nqs_local_energy_workspace_size, C.byref(model.c), ns, C.byref(ham.c), p))
+    eloc = torch.empty(ns, dtype=torch.complex128, device=configs.device)
+    check(lib.nqs_local_energy(C.byref(model.c), _ptr(theta), _ptr(configs), ns, C.byref(ham.c), p, _ptr(eloc),
+                               ws.h, _stream()))
+    if sync:
+        ws.sync_status()
+    return eloc
+
+
+def nqs_connections(configs: torch.Tensor, ham: Hamiltonian, ws: Optional[Workspace] = None):
+    """(count int32 [n_s], offset int64 [n_s+1], bond int32 [n_conn])."""
+    lib = _lib.load()
+    ns = int(configs.shape[0])
+    maxc = ns * int(ham.c.n_bonds)
+    ws = ws or Workspace()
+    ws.ensure(4 * maxc + 1024)
+    cnt = torch.empty(ns, dtype=torch.int32, device=configs.device)
+    off = torch.empty(ns + 1, dtype=torch.int64, device=configs.device)
+    bond = torch.empty(max(maxc, 1), dtype=torch.int32, device=configs.device)
+    n = C.c_int64(0)
+    check(lib.nqs_connections(_ptr(configs), ns, C.byref(ham.c), _ptr(cnt), _ptr(off), _ptr(bond), maxc,
+                              C.byref(n), ws.h, _stream()))
+    ws.sync_status()
+    return cnt, off, bond[: n.value]
+
+
+def qgt_block_build(O: torch.Tensor, n_s: int, block_off, eloc: torch.Tensor, precision="fp64",
+                    w: Optional[torch.Tensor] = None, ws: Optional[Workspace] = None, sync: bool = True):
+    """(S_packed c128, F c128 [n_p], Omean c128 [n_p], Emean c128 [1]). O is overwritten
+    with the centred dO in fp64/fp32 modes."""
+    lib = _lib.load()
+    p = _prec(precision)
+    off = _off(block_off)
+    nb = len(off) - 1
+    n_p = int(block_off[-1])
+    ldo = int(O.shape[1])
+    ws = ws or Workspace()
+    ws.ensure(_size(lib.qgt_block_build_workspace_size, n_s, n_p, off, nb, p))
+    dev = O.device
+    S = torch.zeros(int(lib.qgt_packed_size(off, nb)), dtype=torch.complex128, device=dev)
+    F = torch.empty(n_p, dtype=torch.complex128, device=dev)
+    Om = torch.empty(n_p, dtype=torch.complex128, device=dev)
+    Em = torch.empty(1, dtype=torch.complex128, device=dev)
+    check(lib.qgt_block_build(_ptr(O), ldo, n_s, n_p, _ptr(w), off, nb, _ptr(eloc), p, _ptr(S), _ptr(F),
+                              _ptr(Om), _ptr(Em), ws.h, _stream()))
+    if sync:
+        ws.sync_status()
+    return S, F, Om, Em
+
+
+def qgt_block_solve(S: torch.Tensor, block_off, F: torch.Tensor, diag_shift: float, cutoff: float,
+                    cutoff_mode: int = 0, eta: float = 1.0, want_evals: bool = True,
+                    ws: Optional[Workspace] = None, sync: bool = True):
+    """(dtheta c128 [n_p], evals f64 [n_p] or None, n_kept int32 [n_blocks]). S is overwritten."""
+    lib = _lib.load()
+    off = _off(block_off)
+    nb = len(off) - 1
+    n_p = int(block_off[-1])
+    ws = ws or Workspace()
+    ws.ensure(_size(lib.qgt_block_solve_workspace_size, off, nb))
+    dev = S.device
+    dth = torch.empty(n_p, dtype=torch.complex128, device=dev)
+    ev = torch.empty(n_p, dtype=torch.float64, device=dev) if want_evals else None
+    nk = torch.empty(nb, dtype=torch.int32, device=dev)
+    check(lib.qgt_block_solve(_ptr(S), off, nb, _ptr(F), float(diag_shift), float(cutoff), int(cutoff_mode),
+                              float(eta), _ptr(dth), _ptr(ev), _ptr(nk), ws.h, _stream()))
+    if sync:
+        ws.sync_status()
+    return dth, ev, nk
+
+
+class SRStep:
+    """A prepared block-layer SR step: sizes the workspace once, then runs
+    ``sr_step`` on new (theta, configs) of the same shape."""
+
+    def __init__(self, model: Model, n_s: int, ham: Hamiltonian, block_off, precision="split_bf16",
+                 diag_shift: float = 1e-3, cutoff: float = 1e-10, cutoff_mode: int = 0, eta: float = 1.0,
+                 want_evals: bool = False, device="cuda"):
+        lib = _lib.load()
+        self.model, self.ham = model, ham
+        self.n_s = int(n_s)
+        self.p = _prec(precision)
+        self.off = _off(block_off)
+        self.nb = len(self.off) - 1
+        self.n_p = int(block_off[-1])
+        self.shift, self.cutoff, self.mode, self.eta = float(diag_shift), float(cutoff), int(cutoff_mode), float(eta)
+        self.ws = Workspace(_size(lib.sr_step_workspace_size, C.byref(model.c), self.n_s, C.byref(ham.c), self.off,
+                                  self.nb, self.p), device=device)
+        self.dtheta = torch.empty(self.n_p, dtype=torch.complex128, device=device)
+        self.emean = torch.empty(1, dtype=torch.complex128, device=device)
+        self.evals = torch.empty(self.n_p, dtype=torch.float64, device=device) if want_evals else None
+        self.n_kept = torch.empty(self.nb, dtype=torch.int32, device=device)
+
+    STAGES = ("jacobian", "local_energy", "centring_force", "gram", "tridiagonal_reduction", "solve")
+
+    def enable_stage_timing(self, on: bool = True) -> None:
+        check(_lib.load().nqs_stage_timing(self.ws.h, 1 if on else 0))
+
+    def stage_times(self) -> dict:
+        """Milliseconds per stage of the last sr_step with timing enabled."""
+        ms = (C.c_double * 8)()
+        n = C.c_int32(0)
+        check(_lib.load().nqs_stage_times(self.ws.h, ms, 8, C.byref(n)))
+        return {self.STAGES[i]: ms[i] for i in range(n.value)}
+
+    def __call__(self, theta: torch.Tensor, configs: torch.Tensor, sync: bool = False):
+        lib = _lib.load()
+        check(lib.sr_step(C.byref(self.model.c), _ptr(theta), _ptr(configs), self.n_s, C.byref(self.ham.c),
+                          self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p,
+                          _ptr(self.dtheta), _ptr(self.emean), _ptr(self.evals), _ptr(self.n_kept),
+                          NQS_SYNC if sync else 0, self.ws.h, _stream()))
+        return self.dtheta, self.emean
+
+
+def sr_step(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian, block_off,
+            diag_shift: float, cutoff: float, eta: float = 1.0, precision="fp64", cutoff_mode: int = 0,
+            want_evals: bool = True):
+    """One whole block-layer SR step: (dtheta, Emean, evals, n_kept)."""
+    st = SRStep(model, int(configs.shape[0]), ham, block_off, precision, diag_shift, cutoff, cutoff_mode, eta,
+                want_evals, device=configs.device)
+    st(theta, configs, sync=True)
+    return st.dtheta, st.emean, st.evals, st.n_kept
+
+
+def launch_count() -> int:
+    """Kernels launched by libnqs_sr in this process."""
+    return int(_lib.load().nqs_launch_count())
+
+
+def version() -> str:
+    return _lib.load().nqs_version().decode()

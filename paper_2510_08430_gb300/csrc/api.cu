@@ -1,0 +1,543 @@
+// C ABI of libnqs_sr: argument checks, workspace carving and the order of the
+// stages of one block-layer SR step (see include/nqs_sr.h for the contract).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <new>
+#include "internal.cuh"
+
+using namespace nqs;
+
+constexpr int NSTAGE = 6;  // jacobian, local energy, centring+force, gram, tridiagonal reduction, solve
+struct nqs_workspace {
+    char* base;
+    size_t bytes;
+    bool timing;
+    bool recorded;
+    cudaEvent_t ev[NSTAGE + 1];
+};
+
+unsigned long long& nqs::launch_counter() {
+    static unsigned long long n = 0;
+    return n;
+}
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(NQS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                               \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return cuda_fail(_e, where); \
+    } while (0)
+
+constexpr size_t STATUS_BYTES = 256;
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bump allocator over the caller's workspace (after the status header).
+struct Arena {
+    char* base;
+    size_t cap, used;
+    void* take(size_t bytes) {
+        void* p = base ? base + used : nullptr;
+        used += al256(bytes);
+        return p;
+    }
+};
+Arena arena_of(nqs_workspace* ws) {
+    Arena a;
+    a.base = ws ? ws->base + STATUS_BYTES : nullptr;
+    a.cap = ws ? (ws->bytes > STATUS_BYTES ? ws->bytes - STATUS_BYTES : 0) : 0;
+    a.used = 0;
+    return a;
+}
+Arena sizing_arena() { return Arena{nullptr, 0, 0}; }
+
+DevStatus* status_of(nqs_workspace* ws) { return reinterpret_cast<DevStatus*>(ws->base); }
+
+inline size_t csize(int prec) { return prec == NQS_FP64 ? sizeof(c128) : sizeof(c64); }
+inline int nsplit_of(int prec) { return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : 0); }
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+int check_prec(int prec) {
+    if (prec != NQS_FP64 && prec != NQS_FP32 && prec != NQS_SPLIT_BF16 && prec != NQS_SPLIT_BF16X3)
+        return fail(NQS_ERR_INVALID_ARG, "unknown precision %d", prec);
+    return NQS_OK;
+}
+
+int check_offsets(const int64_t* off, int nb, long long np) {
+    if (!off || nb < 1) return fail(NQS_ERR_INVALID_ARG, "block_off is NULL or n_blocks < 1");
+    if (nb > MAXB) return fail(NQS_ERR_INVALID_ARG, "n_blocks %d exceeds the limit %d", nb, MAXB);
+    if (off[0] != 0) return fail(NQS_ERR_INVALID_ARG, "block_off[0] must be 0");
+    for (int b = 0; b < nb; ++b)
+        if (off[b + 1] <= off[b]) return fail(NQS_ERR_INVALID_ARG, "block_off not strictly increasing at %d", b);
+    if (np >= 0 && off[nb] != np)
+        return fail(NQS_ERR_INVALID_ARG, "block_off[n_blocks] = %lld != n_p = %lld", (long long)off[nb], np);
+    return NQS_OK;
+}
+
+int ham_desc(const nqs_hamiltonian* h, int n_sites, HamDesc* hd) {
+    if (!h || !h->bond_ij || !h->bond_J) return fail(NQS_ERR_INVALID_ARG, "hamiltonian or bond arrays NULL");
+    if (h->n_sites != n_sites) return fail(NQS_ERR_INVALID_ARG, "hamiltonian has %d sites, model %d", h->n_sites, n_sites);
+    if (h->n_bonds < 1 || h->n_bonds > 16 * MAXN) return fail(NQS_ERR_INVALID_ARG, "bad n_bonds %d", h->n_bonds);
+    if (h->sign_rule != 1 && h->sign_rule != -1) return fail(NQS_ERR_INVALID_ARG, "sign_rule must be +-1");
+    hd->n_sites = h->n_sites;
+    hd->n_bonds = h->n_bonds;
+    hd->bond_ij = h->bond_ij;
+    hd->bond_J = h->bond_J;
+    hd->c = h->c;
+    hd->sign_rule = h->sign_rule;
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------ stage plans
+struct JacBufs {
+    void *thR, *wtR, *Z, *G;
+    c128* logpsi;
+};
+void plan_model(Arena& a, const ModelDesc& md, long long ns, int prec, JacBufs* b, bool need_G) {
+    const size_t cs = csize(prec);
+    b->thR = a.take(cs * md.n_p);
+    b->wtR = a.take(cs * (size_t)(model_wt_elems(md) > 0 ? model_wt_elems(md) : 1));
+    b->Z = a.take(cs * (size_t)model_z_elems(md, ns));
+    b->G = need_G ? a.take(cs * (size_t)model_z_elems(md, ns)) : nullptr;
+    b->logpsi = static_cast<c128*>(a.take(sizeof(c128) * ns));
+}
+
+struct ElocBufs {
+    int32_t *cnt, *cbond, *csamp;
+    long long* off;
+    c128* terms;
+};
+void plan_eloc(Arena& a, long long ns, int nbonds, ElocBufs* b) {
+    const long long maxc = ns * nbonds;
+    b->cnt = static_cast<int32_t*>(a.take(4 * ns));
+    b->off = static_cast<long long*>(a.take(8 * (ns + 1)));
+    b->cbond = static_cast<int32_t*>(a.take(4 * maxc));
+    b->csamp = static_cast<int32_t*>(a.take(4 * maxc));
+    b->terms = static_cast<c128*>(a.take(16 * maxc));
+}
+
+struct BuildBufs {
+    c128* e;
+    void* planes[3];
+    long long ldk;
+};
+void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
+    b->e = static_cast<c128*>(a.take(16 * ns));
+    b->ldk = round_up(ns, 64);
+    const int nsp = nsplit_of(prec);
+    for (int i = 0; i < 3; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
+}
+
+// ------------------------------------------------------------------ stages
+int run_model(const ModelDesc& md, int prec, const void* theta, const int8_t* x, long long ns,
+              const JacBufs& b, cudaStream_t st) {
+    CK(launch_prepare_params(prec, md, theta, b.thR, b.wtR, st), "prepare_params");
+    CK(launch_forward(prec, md, b.thR, b.wtR, x, ns, b.Z, b.logpsi, st), "forward");
+    return NQS_OK;
+}
+
+int run_eloc(const ModelDesc& md, int prec, const HamDesc& hd, const int8_t* x, long long ns,
+             const JacBufs& jb, const ElocBufs& eb, c128* eloc, DevStatus* status, cudaStream_t st) {
+    CK(launch_conn_count(x, ns, hd, eb.cnt, st), "conn_count");
+    CK(launch_scan(eb.cnt, ns, eb.off, st), "scan");
+    CK(launch_conn_fill(x, ns, hd, eb.off, eb.cbond, eb.csamp, st), "conn_fill");
+    CK(launch_conn_terms(prec, md, jb.thR, jb.wtR, jb.Z, jb.logpsi, x, hd, eb.cbond, eb.csamp, eb.off + ns,
+                         ns * hd.n_bonds, eb.terms, st),
+       "conn_terms");
+    CK(launch_eloc_reduce(x, ns, hd, eb.off, eb.terms, eloc, status, st), "eloc_reduce");
+    return NQS_OK;
+}
+
+int run_build(void* O, long long ldo, long long ns, long long np, const double* w, const int64_t* off, int nb,
+              const c128* eloc, int prec, c128* S, c128* F, c128* Omean, c128* Emean, const BuildBufs& bb,
+              DevStatus* status, cudaStream_t st, cudaEvent_t gram_event = nullptr) {
+    CK(launch_emean(eloc, w, ns, Emean, bb.e, status, st), "emean");
+    const int nsp = nsplit_of(prec);
+    CK(launch_center(prec, nsp, O, ldo, ns, np, w, bb.e, F, Omean, nsp ? bb.planes : nullptr, bb.ldk, status, st),
+       "center");
+    if (gram_event) CK(cudaEventRecord(gram_event, st), "event");
+    GramTable* tab = new (std::nothrow) GramTable;
+    if (!tab) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    const double scale = w ? 1.0 : 1.0 / (double)ns;
+    cudaError_t e;
+    if (nsp) {
+        gram_table(off, nb, 64, tab);
+        e = launch_gram_tc(nsp, bb.planes, 2 * np, bb.ldk, bb.ldk, GRAM_K_CHUNK, scale, *tab, S, status, st);
+    } else {
+        gram_table(off, nb, 64, tab);
+        e = launch_gram_simt(prec, O, ldo, ns, w, scale, *tab, S, st);
+    }
+    delete tab;
+    if (e == cudaErrorNotSupported) return fail(NQS_ERR_UNSUPPORTED, "tensor-core Gram needs an sm_103 device");
+    CK(e, "gram");
+    return NQS_OK;
+}
+
+int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, double cutoff, int mode,
+              double eta, c128* dtheta, double* evals, int32_t* n_kept, Arena& a, DevStatus* status,
+              cudaStream_t st, cudaEvent_t trd_event = nullptr) {
+    if (!(shift >= 0.0)) return fail(NQS_ERR_INVALID_ARG, "diag_shift must be >= 0");
+    if (!(cutoff >= 0.0)) return fail(NQS_ERR_INVALID_ARG, "cutoff must be >= 0");
+    if (mode != 0 && mode != 1) return fail(NQS_ERR_INVALID_ARG, "cutoff_mode must be 0 or 1");
+    const size_t need = solve_workspace_bytes(off, nb);
+    void* work = a.take(need);
+    SolveArgs sa{shift, cutoff, eta, mode, evals != nullptr, trd_event};
+    const int rc = launch_block_solve(S, off, nb, F, sa, dtheta, evals, n_kept, work, need, status, st);
+    if (rc == NQS_ERR_UNSUPPORTED) return fail(rc, "block larger than the solver limit");
+    if (rc != NQS_OK) return fail(rc, "block solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return NQS_OK;
+}
+
+int check_ws(nqs_workspace* ws, const Arena& need) {
+    if (!ws) return fail(NQS_ERR_INVALID_ARG, "workspace is NULL");
+    const size_t total = need.used + STATUS_BYTES;
+    if (ws->bytes < total)
+        return fail(NQS_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws->bytes, total);
+    return NQS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nqs_last_error(void) { return g_err.c_str(); }
+const char* nqs_version(void) { return "nqs_sr 0.1 (sm_103a)"; }
+
+int nqs_workspace_create(void* device_ptr, size_t bytes, nqs_workspace** ws) {
+    if (!ws || !device_ptr) return fail(NQS_ERR_INVALID_ARG, "NULL workspace pointer");
+    if (reinterpret_cast<uintptr_t>(device_ptr) % 256) return fail(NQS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    if (bytes < STATUS_BYTES) return fail(NQS_ERR_WORKSPACE, "workspace smaller than %zu bytes", STATUS_BYTES);
+    nqs_workspace* w = new (std::nothrow) nqs_workspace;
+    if (!w) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    w->base = static_cast<char*>(device_ptr);
+    w->bytes = bytes;
+    w->timing = false;
+    w->recorded = false;
+    for (int i = 0; i <= NSTAGE; ++i) w->ev[i] = nullptr;
+    cudaError_t e = cudaMemset(w->base, 0, STATUS_BYTES);
+    if (e != cudaSuccess) {
+        delete w;
+        return cuda_fail(e, "workspace status init");
+    }
+    *ws = w;
+    return NQS_OK;
+}
+
+int nqs_workspace_destroy(nqs_workspace* ws) {
+    if (ws) {
+        for (int i = 0; i <= NSTAGE; ++i)
+            if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
+    }
+    delete ws;
+    return NQS_OK;
+}
+
+int nqs_stage_timing(nqs_workspace* ws, int32_t enable) {
+    if (!ws) return fail(NQS_ERR_INVALID_ARG, "workspace is NULL");
+    if (enable && !ws->ev[0]) {
+        for (int i = 0; i <= NSTAGE; ++i) CK(cudaEventCreate(&ws->ev[i]), "event create");
+    }
+    ws->timing = enable != 0;
+    ws->recorded = false;
+    return NQS_OK;
+}
+
+int nqs_stage_times(nqs_workspace* ws, double* ms_out, int32_t max_stages, int32_t* n_stages) {
+    if (!ws || !ms_out || !n_stages) return fail(NQS_ERR_INVALID_ARG, "NULL argument");
+    if (!ws->recorded) return fail(NQS_ERR_INVALID_ARG, "no timed sr_step since timing was enabled");
+    CK(cudaEventSynchronize(ws->ev[NSTAGE]), "event sync");
+    const int n = max_stages < NSTAGE ? max_stages : NSTAGE;
+    for (int i = 0; i < n; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ws->ev[i], ws->ev[i + 1]), "elapsed");
+        ms_out[i] = ms;
+    }
+    *n_stages = n;
+    return NQS_OK;
+}
+
+int64_t nqs_launch_count(void) { return (int64_t)__atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); }
+
+int nqs_sync_status(nqs_workspace* ws, void* stream) {
+    if (!ws) return fail(NQS_ERR_INVALID_ARG, "workspace is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus h;
+    CK(cudaMemcpyAsync(&h, ws->base, sizeof h, cudaMemcpyDeviceToHost, st), "status read");
+    CK(cudaStreamSynchronize(st), "stream sync");
+    if (h.code != 0) {
+        CK(cudaMemsetAsync(ws->base, 0, sizeof(DevStatus), st), "status clear");
+        CK(cudaStreamSynchronize(st), "stream sync");
+        return fail(h.code, "device reported status %d in stage %d (detail %lld)", h.code, h.where, h.detail);
+    }
+    return NQS_OK;
+}
+
+int64_t qgt_packed_size(const int64_t* block_off, int32_t n_blocks) {
+    if (!block_off || n_blocks < 1) return -1;
+    int64_t t = 0;
+    for (int b = 0; b < n_blocks; ++b) t += (block_off[b + 1] - block_off[b]) * (block_off[b + 1] - block_off[b]);
+    return t;
+}
+
+// ---------------------------------------------------------------- sizes
+int nqs_jacobian_workspace_size(const nqs_model* m, int64_t n_s, int32_t precision, size_t* bytes) {
+    ModelDesc md;
+    if (!bytes || n_s < 1 || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    Arena a = sizing_arena();
+    JacBufs jb;
+    plan_model(a, md, n_s, precision, &jb, true);
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+int nqs_local_energy_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonian* h, int32_t precision,
+                                    size_t* bytes) {
+    ModelDesc md;
+    if (!bytes || n_s < 1 || !h || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    Arena a = sizing_arena();
+    JacBufs jb;
+    plan_model(a, md, n_s, precision, &jb, false);
+    ElocBufs eb;
+    plan_eloc(a, n_s, h->n_bonds, &eb);
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+int qgt_block_build_workspace_size(int64_t n_s, int64_t n_p, const int64_t* block_off, int32_t n_blocks,
+                                   int32_t precision, size_t* bytes) {
+    if (!bytes || n_s < 1 || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
+    int rc = check_offsets(block_off, n_blocks, n_p);
+    if (rc) return rc;
+    Arena a = sizing_arena();
+    BuildBufs bb;
+    plan_build(a, n_s, n_p, precision, &bb);
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+int qgt_block_solve_workspace_size(const int64_t* block_off, int32_t n_blocks, size_t* bytes) {
+    if (!bytes) return fail(NQS_ERR_INVALID_ARG, "bytes is NULL");
+    int rc = check_offsets(block_off, n_blocks, -1);
+    if (rc) return rc;
+    *bytes = al256(solve_workspace_bytes(block_off, n_blocks)) + STATUS_BYTES;
+    return NQS_OK;
+}
+
+static void plan_step(Arena& a, const ModelDesc& md, long long ns, int nbonds, const int64_t* off, int nb, int prec,
+                      JacBufs* jb, ElocBufs* eb, BuildBufs* bb, void** O, long long* ldo, c128** eloc, c128** F,
+                      c128** S) {
+    plan_model(a, md, ns, prec, jb, true);
+    plan_eloc(a, ns, nbonds, eb);
+    plan_build(a, ns, md.n_p, prec, bb);
+    *ldo = round_up(ns, 32);
+    *O = a.take(csize(prec) * (size_t)md.n_p * (size_t)(*ldo));
+    *eloc = static_cast<c128*>(a.take(16 * ns));
+    *F = static_cast<c128*>(a.take(16 * (size_t)md.n_p));
+    long long sz = 0;
+    for (int b = 0; b < nb; ++b) sz += (off[b + 1] - off[b]) * (off[b + 1] - off[b]);
+    *S = static_cast<c128*>(a.take(16 * (size_t)sz));
+}
+
+int sr_step_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonian* h, const int64_t* block_off,
+                           int32_t n_blocks, int32_t precision, size_t* bytes) {
+    ModelDesc md;
+    if (!bytes || n_s < 1 || !h || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    int rc = check_offsets(block_off, n_blocks, md.n_p);
+    if (rc) return rc;
+    Arena a = sizing_arena();
+    JacBufs jb;
+    ElocBufs eb;
+    BuildBufs bb;
+    void* O;
+    long long ldo;
+    c128 *eloc, *F, *S;
+    plan_step(a, md, n_s, h->n_bonds, block_off, n_blocks, precision, &jb, &eb, &bb, &O, &ldo, &eloc, &F, &S);
+    a.take(solve_workspace_bytes(block_off, n_blocks));
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+// ---------------------------------------------------------------- compute calls
+int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s, int32_t precision,
+                 void* logpsi_out, void* O_out, int64_t ldo, nqs_workspace* ws, void* stream) {
+    ModelDesc md;
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (n_s < 1 || !theta || !configs || !logpsi_out || !O_out || ldo < n_s)
+        return fail(NQS_ERR_INVALID_ARG, "nqs_jacobian: NULL pointer, n_s < 1 or ldo < n_s");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    Arena a = arena_of(ws);
+    JacBufs jb;
+    plan_model(a, md, n_s, precision, &jb, true);
+    int rc = check_ws(ws, a);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rp = precision == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    rc = run_model(md, rp, theta, configs, n_s, jb, st);
+    if (rc) return rc;
+    CK(launch_backward(rp, md, jb.thR, jb.Z, n_s, jb.G, st), "backward");
+    CK(launch_jac_write(rp, md, jb.Z, jb.G, configs, n_s, O_out, ldo, st), "jacobian");
+    CK(cudaMemcpyAsync(logpsi_out, jb.logpsi, sizeof(c128) * n_s, cudaMemcpyDeviceToDevice, st), "logpsi copy");
+    return NQS_OK;
+}
+
+int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
+                     const nqs_hamiltonian* h, int32_t precision, void* eloc_out, nqs_workspace* ws, void* stream) {
+    ModelDesc md;
+    HamDesc hd;
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (n_s < 1 || !theta || !configs || !eloc_out) return fail(NQS_ERR_INVALID_ARG, "nqs_local_energy: bad arguments");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    int rc = ham_desc(h, md.N, &hd);
+    if (rc) return rc;
+    Arena a = arena_of(ws);
+    JacBufs jb;
+    plan_model(a, md, n_s, precision, &jb, false);
+    ElocBufs eb;
+    plan_eloc(a, n_s, hd.n_bonds, &eb);
+    rc = check_ws(ws, a);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rp = precision == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    rc = run_model(md, rp, theta, configs, n_s, jb, st);
+    if (rc) return rc;
+    return run_eloc(md, rp, hd, configs, n_s, jb, eb, static_cast<c128*>(eloc_out), status_of(ws), st);
+}
+
+int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h, int32_t* conn_count,
+                    int64_t* conn_offset, int32_t* conn_bond, int64_t max_conn, int64_t* n_conn_out,
+                    nqs_workspace* ws, void* stream) {
+    HamDesc hd;
+    if (!configs || n_s < 1 || !conn_count || !conn_offset || !conn_bond || !n_conn_out)
+        return fail(NQS_ERR_INVALID_ARG, "nqs_connections: bad arguments");
+    if (!h) return fail(NQS_ERR_INVALID_ARG, "hamiltonian is NULL");
+    int rc = ham_desc(h, h->n_sites, &hd);
+    if (rc) return rc;
+    if (hd.n_sites < 2 || hd.n_sites > MAXN) return fail(NQS_ERR_INVALID_ARG, "bad n_sites");
+    Arena a = arena_of(ws);
+    int32_t* csamp = static_cast<int32_t*>(a.take(4 * (size_t)(max_conn > 0 ? max_conn : 1)));
+    rc = check_ws(ws, a);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(launch_conn_count(configs, n_s, hd, conn_count, st), "conn_count");
+    CK(launch_scan(conn_count, n_s, reinterpret_cast<long long*>(conn_offset), st), "scan");
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, conn_offset + n_s, sizeof total, cudaMemcpyDeviceToHost, st), "total read");
+    CK(cudaStreamSynchronize(st), "sync");
+    *n_conn_out = total;
+    if (total > max_conn) return fail(NQS_ERR_INVALID_ARG, "max_conn %lld < %lld connections", (long long)max_conn, total);
+    CK(launch_conn_fill(configs, n_s, hd, reinterpret_cast<const long long*>(conn_offset), conn_bond, csamp, st),
+       "conn_fill");
+    return NQS_OK;
+}
+
+int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const double* w, const int64_t* block_off,
+                    int32_t n_blocks, const void* eloc, int32_t precision, void* S_packed, void* F_out,
+                    void* Omean_out, void* Emean_out, nqs_workspace* ws, void* stream) {
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (!O || !eloc || !S_packed || !F_out || n_s < 1 || n_p < 1 || ldo < n_s)
+        return fail(NQS_ERR_INVALID_ARG, "qgt_block_build: bad arguments");
+    int rc = check_offsets(block_off, n_blocks, n_p);
+    if (rc) return rc;
+    Arena a = arena_of(ws);
+    BuildBufs bb;
+    plan_build(a, n_s, n_p, precision, &bb);
+    rc = check_ws(ws, a);
+    if (rc) return rc;
+    return run_build(O, ldo, n_s, n_p, w, block_off, n_blocks, static_cast<const c128*>(eloc), precision,
+                     static_cast<c128*>(S_packed), static_cast<c128*>(F_out), static_cast<c128*>(Omean_out),
+                     static_cast<c128*>(Emean_out), bb, status_of(ws), static_cast<cudaStream_t>(stream));
+}
+
+int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, const void* F, double diag_shift,
+                    double cutoff, int32_t cutoff_mode, double eta, void* dtheta_out, double* evals_out,
+                    int32_t* n_kept_out, nqs_workspace* ws, void* stream) {
+    if (!S_packed || !F || !dtheta_out) return fail(NQS_ERR_INVALID_ARG, "qgt_block_solve: NULL pointer");
+    int rc = check_offsets(block_off, n_blocks, -1);
+    if (rc) return rc;
+    Arena a = arena_of(ws);
+    Arena need = sizing_arena();
+    need.take(solve_workspace_bytes(block_off, n_blocks));
+    rc = check_ws(ws, need);
+    if (rc) return rc;
+    return run_solve(static_cast<c128*>(S_packed), block_off, n_blocks, static_cast<const c128*>(F), diag_shift,
+                     cutoff, cutoff_mode, eta, static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a,
+                     status_of(ws), static_cast<cudaStream_t>(stream));
+}
+
+int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h,
+            const int64_t* block_off, int32_t n_blocks, double diag_shift, double cutoff, int32_t cutoff_mode,
+            double eta, int32_t precision, void* dtheta_out, void* Emean_out, double* evals_out,
+            int32_t* n_kept_out, int32_t flags, nqs_workspace* ws, void* stream) {
+    ModelDesc md;
+    HamDesc hd;
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (n_s < 1 || !theta || !configs || !dtheta_out || !Emean_out)
+        return fail(NQS_ERR_INVALID_ARG, "sr_step: bad arguments");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    int rc = ham_desc(h, md.N, &hd);
+    if (rc) return rc;
+    rc = check_offsets(block_off, n_blocks, md.n_p);
+    if (rc) return rc;
+    Arena a = arena_of(ws);
+    JacBufs jb;
+    ElocBufs eb;
+    BuildBufs bb;
+    void* O;
+    long long ldo;
+    c128 *eloc, *F, *S;
+    plan_step(a, md, n_s, hd.n_bonds, block_off, n_blocks, precision, &jb, &eb, &bb, &O, &ldo, &eloc, &F, &S);
+    Arena need = a;
+    need.take(solve_workspace_bytes(block_off, n_blocks));
+    rc = check_ws(ws, need);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* status = status_of(ws);
+    const int rp = precision == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    const bool tm = ws->timing;
+    if (tm) CK(cudaEventRecord(ws->ev[0], st), "event");
+    rc = run_model(md, rp, theta, configs, n_s, jb, st);
+    if (rc) return rc;
+    CK(launch_backward(rp, md, jb.thR, jb.Z, n_s, jb.G, st), "backward");
+    CK(launch_jac_write(rp, md, jb.Z, jb.G, configs, n_s, O, ldo, st), "jacobian");
+    if (tm) CK(cudaEventRecord(ws->ev[1], st), "event");
+    rc = run_eloc(md, rp, hd, configs, n_s, jb, eb, eloc, status, st);
+    if (rc) return rc;
+    if (tm) CK(cudaEventRecord(ws->ev[2], st), "event");
+    rc = run_build(O, ldo, n_s, md.n_p, nullptr, block_off, n_blocks, eloc, precision, S, F, nullptr,
+                   static_cast<c128*>(Emean_out), bb, status, st, tm ? ws->ev[3] : nullptr);
+    if (rc) return rc;
+    if (tm) CK(cudaEventRecord(ws->ev[4], st), "event");
+    rc = run_solve(S, block_off, n_blocks, F, diag_shift, cutoff, cutoff_mode, eta, static_cast<c128*>(dtheta_out),
+                   evals_out, n_kept_out, a, status, st, tm ? ws->ev[5] : nullptr);
+    if (rc) return rc;
+    if (tm) {
+        CK(cudaEventRecord(ws->ev[6], st), "event");
+        ws->recorded = true;
+    }
+    if (flags & NQS_SYNC) return nqs_sync_status(ws, stream);
+    return NQS_OK;
+}
+
+}  // extern "C"

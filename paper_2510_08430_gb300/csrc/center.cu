@@ -1,0 +1,158 @@
+// Means, centring and force (second form of Eq. 2; Sec. 2 force):
+//   <E> = sum_s w_s E_loc(s),  e_s = E_loc(s) - <E>,
+//   <O_k> = sum_s w_s O_k(s),  dO_k(s) = O_k(s) - <O_k>,
+//   F_k = sum_s w_s conj(dO_k(s)) e_s.
+// One CTA per parameter row (a contiguous run of samples): pass 1 reduces the
+// mean, pass 2 re-reads the row (from L2) to write dO and reduce F. All sums
+// accumulate in FP64. In split mode pass 2 writes BF16 hi/lo planes of dO
+// (rows 2k = Re, 2k+1 = Im; sqrt(w_s) folded in when weights are given) for
+// the tensor-core Gram instead of writing dO back.
+#include <cuda_bf16.h>
+#include "internal.cuh"
+
+namespace nqs {
+
+__global__ void __launch_bounds__(1024) emean_kernel(const c128* __restrict__ eloc, const double* __restrict__ w,
+                                                      long long ns, c128* __restrict__ emean,
+                                                      c128* __restrict__ e, DevStatus* status) {
+    __shared__ double sh[32];
+    __shared__ double res[2];
+    double re = 0.0, im = 0.0;
+    const double u = 1.0 / (double)ns;
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+        const double ws = w ? w[s] : u;
+        re = fma(ws, eloc[s].re, re);
+        im = fma(ws, eloc[s].im, im);
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) {
+        res[0] = re;
+        res[1] = im;
+        if (emean) emean[0] = mk<double>(re, im);
+        if (!isfinite(re) || !isfinite(im)) set_status(status, NQS_ERR_NONFINITE, W_CENTER, -1);
+    }
+    __syncthreads();
+    const c128 m = mk<double>(res[0], res[1]);
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) e[s] = eloc[s] - m;
+}
+
+// Splits x (FP64) into NS BF16 terms x ~ p0 + p1 (+ p2), each the rounding of the remainder.
+template <int NS>
+__device__ __forceinline__ void bf16_split(double x, __nv_bfloat16 (&p)[3]) {
+    double r = x;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        p[i] = __double2bfloat16(r);
+        r -= (double)__bfloat162float(p[i]);
+    }
+}
+
+template <typename R, int NS>  // NS = 0: write dO in place; NS = 2, 3: BF16 split planes
+__global__ void __launch_bounds__(256) center_kernel(cx<R>* __restrict__ O, long long ldo, long long ns,
+                                                      const double* __restrict__ w, const c128* __restrict__ e,
+                                                      c128* __restrict__ F, c128* __restrict__ Omean,
+                                                      __nv_bfloat16* __restrict__ pl0, __nv_bfloat16* __restrict__ pl1,
+                                                      __nv_bfloat16* __restrict__ pl2, long long ldk,
+                                                      DevStatus* status) {
+    __shared__ double sh[32];
+    const long long p = blockIdx.x;
+    cx<R>* row = O + p * ldo;
+    const double u = 1.0 / (double)ns;
+    double mr = 0.0, mi = 0.0;
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+        const cx<R> v = row[s];
+        const double ws = w ? w[s] : 1.0;
+        mr = fma(ws, (double)v.re, mr);
+        mi = fma(ws, (double)v.im, mi);
+    }
+    mr = block_sum(mr, sh);
+    mi = block_sum(mi, sh);
+    if (!w) {
+        mr *= u;
+        mi *= u;
+    }
+    double fr = 0.0, fi = 0.0;
+    if (NS > 0) {
+        __nv_bfloat16* pls[3] = {pl0, pl1, pl2};
+        for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
+            double dr = 0.0, di = 0.0;
+            if (s < ns) {
+                const cx<R> v = row[s];
+                const double ws = w ? w[s] : u;
+                dr = (double)v.re - mr;
+                di = (double)v.im - mi;
+                // F_k += w_s conj(dO) e_s
+                const c128 es = e[s];
+                fr = fma(ws, fma(dr, es.re, di * es.im), fr);
+                fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
+                if (w) {
+                    const double sw = sqrt(ws);
+                    dr *= sw;
+                    di *= sw;
+                }
+            }
+            __nv_bfloat16 qr[3], qi[3];
+            bf16_split<(NS > 0 ? NS : 1)>(dr, qr);
+            bf16_split<(NS > 0 ? NS : 1)>(di, qi);
+#pragma unroll
+            for (int q = 0; q < (NS > 0 ? NS : 1); ++q) {
+                pls[q][(2 * p) * ldk + s] = qr[q];
+                pls[q][(2 * p + 1) * ldk + s] = qi[q];
+            }
+        }
+    } else {
+        for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+            const cx<R> v = row[s];
+            const double ws = w ? w[s] : u;
+            const cx<R> d = mk<R>((R)((double)v.re - mr), (R)((double)v.im - mi));
+            row[s] = d;
+            const c128 es = e[s];
+            fr = fma(ws, fma((double)d.re, es.re, (double)d.im * es.im), fr);
+            fi = fma(ws, fma((double)d.re, es.im, -(double)d.im * es.re), fi);
+        }
+    }
+    fr = block_sum(fr, sh);
+    fi = block_sum(fi, sh);
+    if (threadIdx.x == 0) {
+        F[p] = mk<double>(fr, fi);
+        if (Omean) Omean[p] = mk<double>(mr, mi);
+        if (!(isfinite(mr) && isfinite(mi) && isfinite(fr) && isfinite(fi)))
+            set_status(status, NQS_ERR_NONFINITE, W_CENTER, p);
+    }
+}
+
+cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* emean, c128* e,
+                         DevStatus* status, cudaStream_t st) {
+    count_launch();
+    emean_kernel<<<1, 1024, 0, st>>>(eloc, w, ns, emean, e, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
+                          const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
+                          DevStatus* status, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)np;
+    __nv_bfloat16* p0 = planes ? (__nv_bfloat16*)planes[0] : nullptr;
+    __nv_bfloat16* p1 = planes ? (__nv_bfloat16*)planes[1] : nullptr;
+    __nv_bfloat16* p2 = (planes && nsplit == 3) ? (__nv_bfloat16*)planes[2] : nullptr;
+    if (nsplit == 2) {
+        count_launch();
+        center_kernel<float, 2><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk, status);
+    } else if (nsplit == 3) {
+        count_launch();
+        center_kernel<float, 3><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk, status);
+    } else if (prec == NQS_FP64) {
+        count_launch();
+        center_kernel<double, 0><<<grid, 256, 0, st>>>((c128*)O, ldo, ns, w, e, F, Omean, nullptr, nullptr, nullptr,
+                                                       0, status);
+    } else {
+        count_launch();
+        center_kernel<float, 0><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, nullptr, nullptr, nullptr, 0,
+                                                      status);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nqs

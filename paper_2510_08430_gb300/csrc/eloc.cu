@@ -1,0 +1,327 @@
+// Local energies (Eq. 1) of the bond Hamiltonians of Sec. 3:
+//   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign psi(x^{ij}) / psi(x) ].
+// Integer stage: per sample, the anti-aligned bonds in bond order (warp ballots
+// over a shared-memory bond table) -> counts, exclusive scan, connection list.
+// Float stage: every connected configuration is pushed through the network in
+// tiles of TR rows with activations in shared memory; the first layer is
+// updated incrementally from the stored pre-activation of the parent sample,
+// z' = z - 2 x_i W[:, i] - 2 x_j W[:, j].
+#include "internal.cuh"
+
+namespace nqs {
+
+constexpr int CONN_WARPS = 8;
+
+__global__ void __launch_bounds__(256) conn_count_kernel(const int8_t* __restrict__ x, long long ns,
+                                                          int N, int nb, const int32_t* __restrict__ bij,
+                                                          int32_t* __restrict__ cnt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int2* bonds = reinterpret_cast<int2*>(smem_raw);
+    int8_t* rowbuf = reinterpret_cast<int8_t*>(bonds + nb);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) bonds[b] = make_int2(bij[2 * b], bij[2 * b + 1]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int8_t* row = rowbuf + wid * N;
+    for (long long s = (long long)blockIdx.x * CONN_WARPS + wid; s < ns; s += (long long)gridDim.x * CONN_WARPS) {
+        for (int k = lane; k < N; k += 32) row[k] = x[s * N + k];
+        __syncwarp();
+        int total = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            bool anti = false;
+            if (b < nb) anti = row[bonds[b].x] != row[bonds[b].y];
+            total += __popc(__ballot_sync(0xffffffffu, anti));
+        }
+        if (lane == 0) cnt[s] = total;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) conn_fill_kernel(const int8_t* __restrict__ x, long long ns, int N,
+                                                         int nb, const int32_t* __restrict__ bij,
+                                                         const long long* __restrict__ off,
+                                                         int32_t* __restrict__ cbond, int32_t* __restrict__ csamp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int2* bonds = reinterpret_cast<int2*>(smem_raw);
+    int8_t* rowbuf = reinterpret_cast<int8_t*>(bonds + nb);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) bonds[b] = make_int2(bij[2 * b], bij[2 * b + 1]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int8_t* row = rowbuf + wid * N;
+    for (long long s = (long long)blockIdx.x * CONN_WARPS + wid; s < ns; s += (long long)gridDim.x * CONN_WARPS) {
+        for (int k = lane; k < N; k += 32) row[k] = x[s * N + k];
+        __syncwarp();
+        long long pos = off[s];
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            bool anti = false;
+            if (b < nb) anti = row[bonds[b].x] != row[bonds[b].y];
+            const unsigned m = __ballot_sync(0xffffffffu, anti);
+            if (anti) {
+                const long long at = pos + __popc(m & ((1u << lane) - 1u));
+                cbond[at] = b;
+                csamp[at] = (int32_t)s;
+            }
+            pos += __popc(m);
+        }
+        __syncwarp();
+    }
+}
+
+// Exclusive scan of int32 counts into int64 offsets [ns + 1], one CTA.
+__global__ void __launch_bounds__(1024) scan_kernel(const int32_t* __restrict__ cnt, long long ns,
+                                                     long long* __restrict__ off) {
+    __shared__ long long part[1024];
+    const long long per = (ns + blockDim.x - 1) / blockDim.x;
+    const long long a = threadIdx.x * per;
+    const long long b = (a + per) < ns ? (a + per) : ns;
+    long long sum = 0;
+    for (long long i = a; i < b; ++i) sum += cnt[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+        long long v = (threadIdx.x >= (unsigned)d) ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long run = part[threadIdx.x] - sum;  // exclusive
+    for (long long i = a; i < b; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) off[ns] = part[threadIdx.x];
+}
+
+// Connected-configuration amplitudes ratios: term[c] = 2 c J_b sign exp(ln psi(x') - ln psi(x)).
+template <typename R>
+__global__ void __launch_bounds__(256) conn_terms_kernel(ModelDesc md, const cx<R>* __restrict__ th,
+                                                          const cx<R>* __restrict__ wt,
+                                                          const cx<R>* __restrict__ Z,
+                                                          const c128* __restrict__ logpsi,
+                                                          const int8_t* __restrict__ x, HamDesc h,
+                                                          const int32_t* __restrict__ cbond,
+                                                          const int32_t* __restrict__ csamp,
+                                                          const long long* __restrict__ nconn_ptr, int TR,
+                                                          c128* __restrict__ terms) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = md.maxw;
+    cx<R>* A = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* B = A + (size_t)TR * ld;
+    int* ssamp = reinterpret_cast<int*>(B + (size_t)TR * ld);
+    int* sbond = ssamp + TR;
+    R* sxi = reinterpret_cast<R*>(sbond + TR);
+    R* sxj = sxi + TR;
+    int* si = reinterpret_cast<int*>(sxj + TR);
+    int* sj = si + TR;
+    cx<R>* lpn = reinterpret_cast<cx<R>*>(((uintptr_t)(sj + TR) + 15) & ~(uintptr_t)15);
+    const long long nconn = *nconn_ptr;  // total connections (device-side scan result)
+    const long long c0 = (long long)blockIdx.x * TR;
+    if (c0 >= nconn) return;
+    const int rows = (int)((nconn - c0) < TR ? (nconn - c0) : TR);
+    const int N = md.N;
+    for (int r = threadIdx.x; r < TR; r += blockDim.x) {
+        if (r < rows) {
+            const int s = csamp[c0 + r], b = cbond[c0 + r];
+            const int i = h.bond_ij[2 * b], j = h.bond_ij[2 * b + 1];
+            ssamp[r] = s;
+            sbond[r] = b;
+            si[r] = i;
+            sj[r] = j;
+            sxi[r] = (R)x[(long long)s * N + i];
+            sxj[r] = (R)x[(long long)s * N + j];
+        } else {
+            ssamp[r] = -1;
+            sbond[r] = 0;
+            si[r] = 0;
+            sj[r] = 0;
+            sxi[r] = R(0);
+            sxj[r] = R(0);
+        }
+    }
+    __syncthreads();
+    const int out0 = md.widths[1];
+    const cx<R>* W0T = wt + md.wtoff[0];  // [N][out0]
+    const bool rbm = md.kind == NQS_RBM;
+    const bool linear = (!rbm) && md.L == 1;
+    if (!linear) {
+        // first layer: z' = z - 2 x_i W[:, i] - 2 x_j W[:, j]
+        for (int idx = threadIdx.x; idx < TR * out0; idx += blockDim.x) {
+            const int r = idx / out0, u = idx % out0;
+            cx<R> v = mk<R>(R(0), R(0));
+            if (r < rows) {
+                const cx<R> z = Z[md.zoff[0] + (long long)ssamp[r] * out0 + u];
+                const cx<R> wi = W0T[(long long)si[r] * out0 + u];
+                const cx<R> wj = W0T[(long long)sj[r] * out0 + u];
+                const R ai = R(-2) * sxi[r], aj = R(-2) * sxj[r];
+                const cx<R> zp = mk<R>(z.re + ai * wi.re + aj * wj.re, z.im + ai * wi.im + aj * wj.im);
+                if (rbm) {
+                    // difference of the hidden-unit terms
+                    v = clncosh(zp) - clncosh(z);
+                } else {
+                    v = clncosh(zp);
+                }
+            }
+            A[r * ld + u] = v;
+        }
+        __syncthreads();
+    }
+    if (rbm) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r = wid; r < rows; r += nw) {
+            cx<R> acc = mk<R>(R(0), R(0));
+            for (int u = lane; u < out0; u += 32) acc = acc + A[r * ld + u];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                const cx<R> ai = th[md.aoff + si[r]], aj = th[md.aoff + sj[r]];
+                acc.re += R(-2) * (sxi[r] * ai.re + sxj[r] * aj.re);
+                acc.im += R(-2) * (sxi[r] * ai.im + sxj[r] * aj.im);
+                lpn[r] = acc;  // ln psi(x') - ln psi(x)
+            }
+        }
+    } else if (linear) {
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            const cx<R> wi = th[md.woff[0] + si[r]], wj = th[md.woff[0] + sj[r]];
+            lpn[r] = mk<R>(R(-2) * (sxi[r] * wi.re + sxj[r] * wj.re), R(-2) * (sxi[r] * wi.im + sxj[r] * wj.im));
+        }
+    } else {
+        for (int l = 1; l < md.L; ++l) {
+            const int out = md.widths[l + 1], in = md.widths[l];
+            const cx<R>* W = wt + md.wtoff[l];
+            const cx<R>* bias = th + md.boff[l];
+            const int groups = (TR / 4) * out;
+            const bool last = l == md.L - 1;
+            for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+                const int rg = g / out, j = g % out;
+                cx<R> acc[4];
+                const cx<R> bj = bias[j];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = bj;
+                for (int k = 0; k < in; ++k) {
+                    const cx<R> w = W[(long long)k * out + j];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) cmac(acc[q], A[(4 * rg + q) * ld + k], w);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = 4 * rg + q;
+                    if (last) {
+                        if (r < rows) lpn[r] = acc[q];
+                    } else {
+                        B[r * ld + j] = clncosh(acc[q]);
+                    }
+                }
+            }
+            __syncthreads();
+            cx<R>* t = A;
+            A = B;
+            B = t;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        cx<double> d = ccast<double>(lpn[r]);
+        if (!rbm && !linear) d = d - logpsi[ssamp[r]];
+        const double m = exp(d.re);
+        double sn, cs;
+        sincos(d.im, &sn, &cs);
+        const double f = 2.0 * h.c * h.bond_J[sbond[r]] * (double)h.sign_rule;
+        terms[c0 + r] = mk<double>(f * m * cs, f * m * sn);
+    }
+}
+
+__global__ void eloc_reduce_kernel(const int8_t* __restrict__ x, long long ns, HamDesc h,
+                                   const long long* __restrict__ off, const c128* __restrict__ terms,
+                                   c128* __restrict__ eloc, DevStatus* status) {
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    double diag = 0.0;
+    const int8_t* row = x + s * h.n_sites;
+    for (int b = 0; b < h.n_bonds; ++b) {
+        const int i = h.bond_ij[2 * b], j = h.bond_ij[2 * b + 1];
+        diag += h.bond_J[b] * (double)(row[i] * row[j]);
+    }
+    c128 e = mk<double>(h.c * diag, 0.0);
+    for (long long c = off[s]; c < off[s + 1]; ++c) e = e + terms[c];
+    if (!finite_cx(e)) set_status(status, NQS_ERR_NONFINITE, W_ELOC, s);
+    eloc[s] = e;
+}
+
+// ------------------------------------------------------------------ launchers
+static size_t conn_smem(const HamDesc& h) {
+    return (size_t)h.n_bonds * sizeof(int2) + (size_t)CONN_WARPS * h.n_sites + 16;
+}
+static int conn_grid(long long ns) {
+    long long g = (ns + CONN_WARPS - 1) / CONN_WARPS;
+    return (int)(g < 8192 ? (g < 1 ? 1 : g) : 8192);
+}
+
+cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, int32_t* cnt,
+                              cudaStream_t st) {
+    if (ns <= 0) return cudaSuccess;
+    const size_t sm = conn_smem(h);
+    cudaError_t e = cudaFuncSetAttribute(conn_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    conn_count_kernel<<<conn_grid(ns), 32 * CONN_WARPS, sm, st>>>(x, ns, h.n_sites, h.n_bonds, h.bond_ij, cnt);
+    return cudaGetLastError();
+}
+cudaError_t launch_scan(const int32_t* cnt, long long ns, long long* off, cudaStream_t st) {
+    count_launch();
+    scan_kernel<<<1, 1024, 0, st>>>(cnt, ns, off);
+    return cudaGetLastError();
+}
+cudaError_t launch_conn_fill(const int8_t* x, long long ns, const HamDesc& h, const long long* off,
+                             int32_t* conn_bond, int32_t* conn_sample, cudaStream_t st) {
+    if (ns <= 0) return cudaSuccess;
+    const size_t sm = conn_smem(h);
+    cudaError_t e = cudaFuncSetAttribute(conn_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    conn_fill_kernel<<<conn_grid(ns), 32 * CONN_WARPS, sm, st>>>(x, ns, h.n_sites, h.n_bonds, h.bond_ij, off,
+                                                                 conn_bond, conn_sample);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t conn_terms_t(const ModelDesc& md, const void* thR, const void* wtR, const void* Z,
+                                const c128* logpsi, const int8_t* x, const HamDesc& h,
+                                const int32_t* cb, const int32_t* cs, const long long* nconn_ptr,
+                                long long max_conn, c128* terms, cudaStream_t st) {
+    if (max_conn <= 0) return cudaSuccess;
+    long long tr = 180000LL / (2LL * md.maxw * (long long)sizeof(cx<R>));
+    tr = tr > 32 ? 32 : tr;
+    tr = (tr / 4) * 4;
+    const int TR = tr < 4 ? 4 : (int)tr;
+    const size_t smem = 2ull * TR * md.maxw * sizeof(cx<R>) + (size_t)TR * (4 * sizeof(int) + 2 * sizeof(R)) +
+                        16 + (size_t)TR * sizeof(cx<R>);
+    cudaError_t e = cudaFuncSetAttribute(conn_terms_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = (max_conn + TR - 1) / TR;
+    count_launch();
+    conn_terms_kernel<R><<<(unsigned)grid, 256, smem, st>>>(md, (const cx<R>*)thR, (const cx<R>*)wtR,
+                                                            (const cx<R>*)Z, logpsi, x, h, cb, cs, nconn_ptr, TR,
+                                                            terms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, const void* wtR,
+                              const void* Z, const c128* logpsi, const int8_t* x, const HamDesc& h,
+                              const int32_t* conn_bond, const int32_t* conn_sample,
+                              const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st) {
+    return prec == NQS_FP64
+               ? conn_terms_t<double>(md, thR, wtR, Z, logpsi, x, h, conn_bond, conn_sample, nconn_ptr, max_conn,
+                                      terms, st)
+               : conn_terms_t<float>(md, thR, wtR, Z, logpsi, x, h, conn_bond, conn_sample, nconn_ptr, max_conn,
+                                     terms, st);
+}
+
+cudaError_t launch_eloc_reduce(const int8_t* x, long long ns, const HamDesc& h, const long long* off,
+                               const c128* terms, c128* eloc, DevStatus* status, cudaStream_t st) {
+    if (ns <= 0) return cudaSuccess;
+    count_launch();
+    eloc_reduce_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(x, ns, h, off, terms, eloc, status);
+    return cudaGetLastError();
+}
+
+}  // namespace nqs

@@ -1,0 +1,437 @@
+// Block-layer QGT on the 5th-generation tensor cores (tcgen05), split BF16 (Eq. 3):
+//   S_b = sum_s w_s dO_b(s)^H dO_b(s)
+// computed as the real Gram G = X X^T of the interleaved real rows X[2k] = Re dO_k,
+// X[2k+1] = Im dO_k (samples contiguous, i.e. K-major operands), so that
+//   Re S[k][l] = G[2k][2l] + G[2k+1][2l+1],   Im S[k][l] = G[2k][2l+1] - G[2k+1][2l].
+// Every entry is split x = hi + lo (both BF16) and G ~ Xh Xh^T + Xh Xl^T + Xl Xh^T with
+// FP32 accumulation in tensor memory (three products per K step).
+//
+// Persistent kernel, one CTA per SM, static round-robin over the lower-triangle
+// 128 x 128 tiles of every block. Warp roles: warp 0 issues TMA loads (128B
+// swizzle) into a STAGES-deep ring, warp 1 allocates tensor memory and issues
+// tcgen05.mma, warps 2-5 drain the double-buffered accumulators (tcgen05.ld),
+// combine the 2 x 2 real blocks into complex entries and store FP64 to S.
+// Every mbarrier wait is bounded; on expiry the kernel records NQS_ERR_TIMEOUT,
+// drains its own copies and MMAs, frees tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include "internal.cuh"
+
+namespace nqs {
+
+namespace tc {
+
+constexpr int BM = 128;          // real rows per tile (64 complex)
+constexpr int BK = 64;           // BF16 elements per 128-byte swizzle row
+constexpr int TILE_BYTES = BM * BK * 2;          // 16 KB
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;              // two 128-column FP32 accumulators
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s budget per wait
+
+// NS split planes; products (a-plane, b-plane) whose order sum is < NS.
+template <int NS> struct Split;
+template <> struct Split<2> {
+    static constexpr int STAGES = 3;
+    static constexpr int NPROD = 3;
+    __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
+    __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+template <> struct Split<3> {
+    static constexpr int STAGES = 2;
+    static constexpr int NPROD = 6;
+    // hh, hm, mh, hl, lh, mm
+    __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
+    __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false on timeout or (if abort_flag is not NULL) when another
+// role has aborted. The iteration cap backs up the time budget.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (abort_flag && *abort_flag) return false;
+            if (gtimer() - t0 > WAIT_NS) return false;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups
+// 1024 bytes apart (SBO), descriptor version 1, leading offset unused (1).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                 // LBO (ignored for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;       // SBO
+    d |= (uint64_t)1u << 46;                 // version
+    d |= (uint64_t)2u << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A/B BF16, both K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TileInfo {
+    int b, I, J;
+};
+
+__device__ __forceinline__ TileInfo decode(const GramTable& tab, long long t) {
+    int lo = 0, hi = tab.nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab.b[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const long long r = t - tab.b[lo].tile0;
+    long long i = (long long)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= r) ++i;
+    while (i * (i + 1) / 2 > r) --i;
+    TileInfo ti;
+    ti.b = lo;
+    ti.I = (int)i;
+    ti.J = (int)(r - i * (i + 1) / 2);
+    return ti;
+}
+
+struct Maps {
+    CUtensorMap m[3];
+};
+
+// Work item = (tile, K chunk). The FP32 accumulator of one chunk covers kpc K-blocks
+// (64 samples each); chunk results are summed in FP64 in S by the epilogue.
+template <int NS>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_tc_kernel(const __grid_constant__ Maps maps, const __grid_constant__ GramTable tab, int nkb, int kpc,
+                   double scale, c128* __restrict__ S, DevStatus* status) {
+    using SP = Split<NS>;
+    constexpr int STAGES = SP::STAGES;
+    constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull_bar[a], 1);
+            mbar_init(&tempty_bar[a], 128);
+        }
+        mbar_init(&done_bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+    volatile int* abort_flag = &abort_sh;
+    const long long total = tab.total_tiles;
+    const int nch = (nkb + kpc - 1) / kpc;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            for (int p = 0; p < NS; ++p) asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.m[p]) : "memory");
+            uint32_t q = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const TileInfo ti = decode(tab, t);
+                const GBlk blk = tab.b[ti.b];
+                const int rowA = (int)(2 * blk.row0 + (long long)ti.I * BM);
+                const int rowB = (int)(2 * blk.row0 + (long long)ti.J * BM);
+                const bool diag = ti.I == ti.J;
+                for (int kb = 0; kb < nkb; ++kb, ++q) {
+                    const int s = q % STAGES;
+                    const uint32_t ph = (q / STAGES) & 1u;
+                    if (!mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) { ok = false; break; }
+                    unsigned char* st = ring + (size_t)s * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], (diag ? NS : 2 * NS) * TILE_BYTES);
+                    for (int p = 0; p < NS; ++p)
+                        tma_load_2d(st + p * TILE_BYTES, &maps.m[p], &full_bar[s], kb * BK, rowA);
+                    if (!diag)
+                        for (int p = 0; p < NS; ++p)
+                            tma_load_2d(st + (NS + p) * TILE_BYTES, &maps.m[p], &full_bar[s], kb * BK, rowB);
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                set_status(status, NQS_ERR_TIMEOUT, W_GRAM_TC, 0);
+            }
+            // drain: the last issued phase of every stage must have landed before exit
+            for (uint32_t st = 0; st < (uint32_t)STAGES; ++st) {
+                if (q > st) {
+                    const uint32_t last = st + (uint32_t)STAGES * ((q - 1u - st) / (uint32_t)STAGES);
+                    mbar_wait(&full_bar[st], (last / STAGES) & 1u, nullptr);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_128x128();
+            uint32_t q = 0, it = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const TileInfo ti = decode(tab, t);
+                const bool diag = ti.I == ti.J;
+                for (int c = 0; c < nch && ok; ++c, ++it) {
+                    const uint32_t acc = it & 1u;
+                    const uint32_t tmem_d = tmem_base + acc * 128u;
+                    if (!mbar_wait(&tempty_bar[acc], ((it >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    const int kb0 = c * kpc, kb1 = (kb0 + kpc) < nkb ? (kb0 + kpc) : nkb;
+                    for (int kb = kb0; kb < kb1; ++kb, ++q) {
+                        const int s = q % STAGES;
+                        const uint32_t ph = (q / STAGES) & 1u;
+                        if (!mbar_wait(&full_bar[s], ph, abort_flag)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t base = smem_u32(ring + (size_t)s * STAGE_BYTES);
+                        const uint32_t boff = diag ? 0u : (uint32_t)(NS * TILE_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes inside the swizzle row
+#pragma unroll
+                            for (int pr = 0; pr < SP::NPROD; ++pr) {
+                                const uint32_t aad = base + SP::pa(pr) * TILE_BYTES + off;
+                                const uint32_t bad = base + boff + SP::pb(pr) * TILE_BYTES + off;
+                                const uint32_t first = (kb == kb0 && kk == 0 && pr == 0) ? 0u : 1u;
+                                umma(tmem_d, sdesc(aad), sdesc(bad), idesc, first);
+                            }
+                        }
+                        umma_commit(&empty_bar[s]);  // frees the stage when these MMAs complete
+                    }
+                    if (!ok) break;
+                    umma_commit(&tfull_bar[acc]);
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                set_status(status, NQS_ERR_TIMEOUT, W_GRAM_TC, 1);
+            }
+            // wait for every MMA issued by this thread before tensor memory is freed
+            umma_commit(&done_bar);
+            mbar_wait(&done_bar, 0u, nullptr);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;  // accumulator row (real row within the tile)
+        const int cpar = r & 1;             // 0: Re row, 1: Im row of complex row r/2
+        uint32_t it = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            const TileInfo ti = decode(tab, t);
+            const GBlk blk = tab.b[ti.b];
+            const int n = blk.n;
+            const long long k = (long long)ti.I * (BM / 2) + (r >> 1);
+            c128* Srow = S + blk.s_off + k * n;
+            const bool row_ok = k < n;
+            for (int c = 0; c < nch; ++c, ++it) {
+                const uint32_t acc = it & 1u;
+                if (!mbar_wait(&tfull_bar[acc], (it >> 1) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+#pragma unroll 1
+                for (int chunk = 0; chunk < 4; ++chunk) {
+                    uint32_t v[32];
+                    const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * 128u + chunk * 32u;
+                    tmem_ld32(taddr, v);
+                    // 32 real columns = 8 pairs of complex columns (l0 = 2m, l1 = 2m + 1)
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const float g0 = __uint_as_float(v[4 * m + 0]);  // col (l0, re)
+                        const float g1 = __uint_as_float(v[4 * m + 1]);  // col (l0, im)
+                        const float g2 = __uint_as_float(v[4 * m + 2]);  // col (l1, re)
+                        const float g3 = __uint_as_float(v[4 * m + 3]);  // col (l1, im)
+                        // even lane (Re row) sends its l1 pair, odd lane (Im row) its l0 pair
+                        const float s0 = cpar ? g0 : g2;
+                        const float s1 = cpar ? g1 : g3;
+                        const float y0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+                        const float y1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                        double re, im;
+                        if (cpar == 0) {   // S[k][l0]: g00 = g0, g01 = g1, g10 = y0, g11 = y1
+                            re = (double)g0 + (double)y1;
+                            im = (double)g1 - (double)y0;
+                        } else {           // S[k][l1]: g00 = y0, g01 = y1, g10 = g2, g11 = g3
+                            re = (double)y0 + (double)g3;
+                            im = (double)y1 - (double)g2;
+                        }
+                        const long long l = (long long)ti.J * (BM / 2) + chunk * 16 + 2 * m + cpar;
+                        if (row_ok && l < n) {
+                            c128 o = mk<double>(scale * re, scale * im);
+                            if (c > 0) o = o + Srow[l];
+                            Srow[l] = o;
+                        }
+                    }
+                }
+                fence_before();
+                mbar_arrive(&tempty_bar[acc]);
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            set_status(status, NQS_ERR_TIMEOUT, W_GRAM_TC, 2);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tc
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap* m, const void* base, long long rows, long long ldk) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows, long long ldk, long long kpad,
+                           int k_chunk, double scale, const GramTable& tab, c128* S, DevStatus* status,
+                           cudaStream_t st) {
+    if (tab.total_tiles <= 0) return cudaSuccess;
+    if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (major != 10 || minor != 3) return cudaErrorNotSupported;
+    if (ldk % tc::BK != 0 || kpad % tc::BK != 0 || kpad > ldk || k_chunk < tc::BK) return cudaErrorInvalidValue;
+    tc::Maps maps;
+    for (int p = 0; p < nsplit; ++p) {
+        if (reinterpret_cast<uintptr_t>(planes[p]) & 15) return cudaErrorInvalidValue;
+        if (!make_map(&maps.m[p], planes[p], rows, ldk)) return cudaErrorInvalidValue;
+    }
+    const int nkb = (int)(kpad / tc::BK);
+    const int kpc = k_chunk / tc::BK;
+    const long long grid = tab.total_tiles < sms ? tab.total_tiles : sms;
+    cudaError_t e;
+    if (nsplit == 2) {
+        const size_t smem = (size_t)tc::Split<2>::STAGES * 4 * tc::TILE_BYTES + 1024;
+        e = cudaFuncSetAttribute(tc::gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        tc::gram_tc_kernel<2><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpc, scale, S, status);
+    } else {
+        const size_t smem = (size_t)tc::Split<3>::STAGES * 6 * tc::TILE_BYTES + 1024;
+        e = cudaFuncSetAttribute(tc::gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        tc::gram_tc_kernel<3><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpc, scale, S, status);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nqs

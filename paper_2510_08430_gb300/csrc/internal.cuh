@@ -1,0 +1,109 @@
+// Internal descriptors and launchers shared by the translation units of libnqs_sr.
+#pragma once
+#include "common.cuh"
+
+namespace nqs {
+
+constexpr int MAXL = 32;        // max weight layers
+constexpr int MAXW = 512;       // max layer width
+constexpr int MAXN = 1024;      // max sites
+constexpr int MAXB = 256;       // max blocks per launch table
+
+// Network description resolved for one call (host-built, passed by value).
+struct ModelDesc {
+    int kind;                   // NQS_RBM / NQS_FFNN
+    int L;                      // weight layers (RBM: 1)
+    int N;                      // sites
+    int n_p;
+    int maxw;                   // max over widths (incl. N)
+    int widths[MAXL + 1];
+    long long woff[MAXL];       // W_l offset in theta (out x in, row-major)
+    long long boff[MAXL];       // b_l offset in theta
+    long long wtoff[MAXL];      // W_l^T offset in the transposed-weight copy (in x out)
+    long long zoff[MAXL];       // Z_l offset in the activation store ([n_s][out_l])
+    long long aoff;             // RBM visible bias offset (0)
+};
+
+int build_model_desc(const nqs_model* m, long long ns, ModelDesc* md);  // returns status
+long long model_wt_elems(const ModelDesc& md);     // transposed weight copy size
+long long model_z_elems(const ModelDesc& md, long long ns);
+
+// ---- launchers (return cudaError_t of the launches) ----
+// theta (c128) -> thR (cx<R>) and W^T copies
+cudaError_t launch_prepare_params(int prec, const ModelDesc& md, const void* theta, void* thR,
+                                  void* wtR, cudaStream_t st);
+// forward: activations Z (all layers) and ln psi (c128)
+cudaError_t launch_forward(int prec, const ModelDesc& md, const void* thR, const void* wtR,
+                           const int8_t* x, long long ns, void* Z, c128* logpsi, cudaStream_t st);
+// backward: per hidden layer G_l = dlnpsi/dz_l stored at the Z_l offsets of G
+cudaError_t launch_backward(int prec, const ModelDesc& md, const void* thR, const void* Z,
+                            long long ns, void* G, cudaStream_t st);
+// Jacobian (parameter-major) from Z, G and x
+cudaError_t launch_jac_write(int prec, const ModelDesc& md, const void* Z, const void* G,
+                             const int8_t* x, long long ns, void* O, long long ldo, cudaStream_t st);
+
+// ---- local energy ----
+struct HamDesc {
+    int n_sites, n_bonds;
+    const int32_t* bond_ij;
+    const double* bond_J;
+    double c;
+    int sign_rule;
+};
+cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, int32_t* cnt,
+                              cudaStream_t st);
+cudaError_t launch_scan(const int32_t* cnt, long long ns, long long* off, cudaStream_t st);
+cudaError_t launch_conn_fill(const int8_t* x, long long ns, const HamDesc& h, const long long* off,
+                             int32_t* conn_bond, int32_t* conn_sample, cudaStream_t st);
+cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, const void* wtR,
+                              const void* Z, const c128* logpsi, const int8_t* x, const HamDesc& h,
+                              const int32_t* conn_bond, const int32_t* conn_sample,
+                              const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st);
+cudaError_t launch_eloc_reduce(const int8_t* x, long long ns, const HamDesc& h,
+                               const long long* off, const c128* terms, c128* eloc,
+                               DevStatus* status, cudaStream_t st);
+
+// ---- centring / force ----
+cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* emean, c128* e,
+                         DevStatus* status, cudaStream_t st);
+// nsplit 0: dO written in place (prec FP64/FP32); nsplit 2 or 3: BF16 split planes (O is c64)
+cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
+                          const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
+                          DevStatus* status, cudaStream_t st);
+
+// ---- Gram ----
+struct GBlk {                   // one QGT block of one instance
+    long long row0;             // first parameter row of the block in the operand
+    long long s_off;            // first element of S_b in the packed output
+    int n;                      // block size
+    int tiles;                  // lower-triangle tile count
+    long long tile0;            // prefix of tiles over previous blocks
+};
+struct GramTable {
+    int nb;
+    long long total_tiles;
+    GBlk b[MAXB];
+};
+cudaError_t launch_gram_simt(int prec, const void* dO, long long ldo, long long ns, const double* w,
+                             double scale, const GramTable& tab, c128* S, cudaStream_t st);
+// tcgen05 BF16 split Gram over nsplit planes (2: 3 products, 3: 6 products), FP32 accumulation
+// over K chunks of k_chunk samples summed in FP64; cudaErrorNotSupported off sm_103.
+constexpr int GRAM_K_CHUNK = 1024;
+cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows, long long ldk, long long kpad,
+                           int k_chunk, double scale, const GramTable& tab, c128* S, DevStatus* status,
+                           cudaStream_t st);
+void gram_table(const int64_t* block_off, int nb, int tile_rows, GramTable* tab);
+
+// ---- per-block solve ----
+struct SolveArgs {
+    double shift, cutoff, eta;
+    int cutoff_mode;
+    bool want_evals;
+    cudaEvent_t ev_trd_done;    // recorded after the tridiagonal reduction (or NULL)
+};
+size_t solve_workspace_bytes(const int64_t* block_off, int nb);
+int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
+                       const SolveArgs& a, c128* dtheta, double* evals, int32_t* n_kept,
+                       void* work, size_t work_bytes, DevStatus* status, cudaStream_t st);
+
+}  // namespace nqs

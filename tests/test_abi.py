@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and validates arguments without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"NQS_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_08430_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2510_08430_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    from paper_2510_08430_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.SIGNATURES, n
+
+
+def test_version_and_error_string(lib):
+    assert b"sm_103a" in lib.nqs_version()
+    assert lib.nqs_last_error() is not None
+
+
+def _model(kind, widths):
+    from paper_2510_08430_gb300 import Model
+    return Model(kind, widths)
+
+
+def test_workspace_size_queries(lib):
+    from paper_2510_08430_gb300 import _lib
+    m = _model(1, [36, 64, 64, 1])
+    out = C.c_size_t(0)
+    assert lib.nqs_jacobian_workspace_size(C.byref(m.c), 4096, 1, C.byref(out)) == 0
+    # thR + W^T + Z + G (c64) + logpsi: grows with n_s
+    small = out.value
+    assert lib.nqs_jacobian_workspace_size(C.byref(m.c), 8192, 1, C.byref(out)) == 0
+    assert out.value > small
+    off = (C.c_int64 * 4)(0, 2368, 6528, 6593)
+    assert lib.qgt_packed_size(off, 3) == 2368 ** 2 + 4160 ** 2 + 65 ** 2
+    assert lib.qgt_block_solve_workspace_size(off, 3, C.byref(out)) == 0 and out.value > 0
+    h = _lib.nqs_hamiltonian(36, 144, None, None, 1.0, 1)
+    assert lib.sr_step_workspace_size(C.byref(m.c), 4096, C.byref(h), off, 3, 2, C.byref(out)) == 0
+    assert out.value > 6593 * 4096 * 8
+
+
+def test_invalid_arguments_are_rejected(lib):
+    out = C.c_size_t(0)
+    bad = (C.c_int64 * 4)(0, 10, 10, 20)  # not strictly increasing
+    assert lib.qgt_block_solve_workspace_size(bad, 3, C.byref(out)) == -1
+    assert b"strictly" in lib.nqs_last_error()
+    bad0 = (C.c_int64 * 2)(1, 5)
+    assert lib.qgt_block_solve_workspace_size(bad0, 1, C.byref(out)) == -1
+    m = _model(1, [36, 64, 64, 2])  # FFNN must end in one output
+    assert lib.nqs_jacobian_workspace_size(C.byref(m.c), 16, 0, C.byref(out)) == -1
+    m = _model(1, [36, 64, 1])
+    assert lib.nqs_jacobian_workspace_size(C.byref(m.c), 16, 7, C.byref(out)) == -1  # precision
+    off = (C.c_int64 * 3)(0, 100, 2368)
+    assert lib.qgt_block_build_workspace_size(16, 999, off, 2, 0, C.byref(out)) == -1  # n_p mismatch
+    assert lib.nqs_workspace_create(None, 1024, C.byref(C.c_void_p())) == -1

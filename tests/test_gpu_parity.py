@@ -1,0 +1,177 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes span several tiles with ragged tails; tolerances follow the precision of
+each path: FP64 path 1e-12 relative on intermediate results and 1e-10 on
+dtheta; FP32 path 1e-4 on dtheta; BF16 split path 1e-6 on dtheta.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from gpu_util import dev_inputs, rel, unpack_lower
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def nq():
+    import paper_2510_08430_gb300 as m
+    return m
+
+
+def _oracle_all(w):
+    return oracle.qgt.sr_step(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.block_off, w.diag_shift,
+                              w.cutoff, 1.0, w.c, w.sign_rule)
+
+
+@pytest.mark.parametrize("name,ns,prec,tol", [
+    ("chain10_rbm", 77, "fp64", 1e-12),
+    ("j1j2_6x6_ffnn", 45, "fp64", 1e-12),
+    ("j1j2_6x6_ffnn", 45, "fp32", 1e-5),
+    ("j1j2_10x10_ffnn5", 33, "fp32", 1e-5),
+])
+def test_jacobian_and_logpsi(name, ns, prec, tol):
+    w = W.make_workload(name, ns)
+    model, theta, x, ham = dev_inputs(w)
+    lp, O = nq().nqs_jacobian(model, theta, x, prec, ldo=ns + 5)
+    lp_o, O_o = oracle.nqs.jacobian(w.model, w.theta, w.configs)
+    Og = O.cpu().numpy()
+    assert np.all(Og[:, ns:] == 0)
+    assert rel(lp.cpu().numpy(), lp_o) < tol
+    assert rel(Og[:, :ns].T, O_o) < tol
+    # element-wise relative to the per-parameter scale
+    err = np.abs(Og[:, :ns].T - O_o) / (np.abs(O_o).max(axis=0, keepdims=True) + 1e-300)
+    assert err.max() < 20 * tol
+
+
+@pytest.mark.parametrize("name,ns", [("chain10_rbm", 50), ("j1j2_6x6_ffnn", 37), ("j1j2_10x10_ffnn5", 21)])
+def test_connections_bit_exact(name, ns):
+    w = W.make_workload(name, ns)
+    _, _, x, ham = dev_inputs(w)
+    cnt, off, bond = nq().nqs_connections(x, ham)
+    ref = oracle.hamiltonian.connections(w.configs, w.bond_ij)
+    assert np.array_equal(bond.cpu().numpy(), ref[:, 1].astype(np.int32))
+    assert np.array_equal(np.repeat(np.arange(ns), cnt.cpu().numpy()), ref[:, 0])
+    o = off.cpu().numpy()
+    assert o[0] == 0 and o[-1] == len(ref) and np.array_equal(np.diff(o), cnt.cpu().numpy())
+
+
+@pytest.mark.parametrize("name,ns,prec,tol", [
+    ("chain10_rbm", 64, "fp64", 1e-12),
+    ("j1j2_6x6_ffnn", 40, "fp64", 1e-12),
+    ("j1j2_6x6_ffnn", 40, "fp32", 1e-5),
+    ("j1j2_10x10_ffnn5", 12, "fp32", 1e-5),
+])
+def test_local_energy(name, ns, prec, tol):
+    w = W.make_workload(name, ns)
+    model, theta, x, ham = dev_inputs(w)
+    el = nq().nqs_local_energy(model, theta, x, ham, prec).cpu().numpy()
+    ref = oracle.hamiltonian.local_energy(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.c, w.sign_rule)
+    assert np.max(np.abs(el - ref) / np.maximum(np.abs(ref), 1.0)) < tol
+
+
+def test_local_energy_marshall_sign_and_units():
+    w = W.make_workload("chain10_rbm", 30)
+    import paper_2510_08430_gb300 as m
+    model, theta, x, _ = dev_inputs(w)
+    ham = m.Hamiltonian(10, w.bond_ij, w.bond_j, 0.25, -1)
+    el = m.nqs_local_energy(model, theta, x, ham, "fp64").cpu().numpy()
+    ref = oracle.hamiltonian.local_energy(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, 0.25, -1)
+    assert rel(el, ref) < 1e-12
+
+
+@pytest.mark.parametrize("name,ns,prec,tol", [
+    ("chain10_rbm", 97, "fp64", 1e-12),
+    ("j1j2_6x6_ffnn", 70, "fp64", 1e-12),
+    ("j1j2_6x6_ffnn", 70, "fp32", 1e-5),
+    ("j1j2_6x6_ffnn", 70, "split_bf16", 5e-5),
+    ("j1j2_6x6_ffnn", 70, "split_bf16x3", 2e-5),
+    ("chain10_rbm", 1100, "split_bf16x3", 2e-6),
+])
+def test_qgt_block_build(name, ns, prec, tol):
+    w = W.make_workload(name, ns)
+    model, theta, x, ham = dev_inputs(w)
+    _, O = nq().nqs_jacobian(model, theta, x, prec)
+    el = nq().nqs_local_energy(model, theta, x, ham, prec)
+    S, F, Om, Em = nq().qgt_block_build(O, ns, w.block_off, el, prec)
+    r = _oracle_all(w)
+    Sl = unpack_lower(S.cpu().numpy(), w.block_off)
+    for b, Sb in enumerate(r["S"]):
+        assert rel(Sl[b], np.tril(Sb)) < tol, b
+    assert rel(F.cpu().numpy(), r["F"]) < 10 * tol
+    assert rel(Om.cpu().numpy(), r["o_mean"]) < tol
+    assert abs(Em.cpu().numpy()[0] - r["e_mean"]) < tol * abs(r["e_mean"])
+
+
+def _herm_psd(n, seed, spec):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    S = (q * spec) @ np.conj(q).T
+    return 0.5 * (S + np.conj(S).T)
+
+
+@pytest.mark.parametrize("sizes", [[1, 2, 3], [17, 65, 130], [64, 129, 5]])
+@pytest.mark.parametrize("cutoff,shift", [(1e-12, 1e-3), (1e-3, 1e-7)])
+def test_qgt_block_solve_against_definition(sizes, cutoff, shift):
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    blocks = []
+    for b, n in enumerate(sizes):
+        spec = np.concatenate([np.logspace(-9, 1, n)]) if n > 1 else np.array([0.7])
+        blocks.append(_herm_psd(n, 100 + b, spec))
+    rng = np.random.default_rng(7)
+    F = rng.normal(size=off[-1]) + 1j * rng.normal(size=off[-1])
+    packed = np.concatenate([B.ravel() for B in blocks])
+    S = torch.as_tensor(packed, device="cuda")
+    dth, ev, nk = nq().qgt_block_solve(S, off, torch.as_tensor(F, device="cuda"), shift, cutoff, 0, 0.9)
+    ref, sig, kept = oracle.qgt.block_solve(blocks, F, off, shift, cutoff, 0.9)
+    assert np.array_equal(nk.cpu().numpy(), kept)
+    evg = ev.cpu().numpy()
+    for b in range(len(sizes)):
+        sl = slice(off[b], off[b + 1])
+        np.testing.assert_allclose(evg[sl], sig[b], rtol=0, atol=1e-12 * sig[b].max())
+    assert rel(dth.cpu().numpy(), ref) < 1e-9
+
+
+def test_solve_absolute_cutoff_mode():
+    sizes = [40, 9]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    blocks = [_herm_psd(n, 3 + n, np.logspace(-6, 0, n)) for n in sizes]
+    F = np.random.default_rng(1).normal(size=off[-1]) + 0j
+    S = torch.as_tensor(np.concatenate([B.ravel() for B in blocks]), device="cuda")
+    dth, _, nk = nq().qgt_block_solve(S, off, torch.as_tensor(F, device="cuda"), 1e-8, 3e-3, 1, 1.0)
+    ref, _, kept = oracle.qgt.block_solve(blocks, F, off, 1e-8, 3e-3, 1.0, absolute=True)
+    assert np.array_equal(nk.cpu().numpy(), kept)
+    assert rel(dth.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("name,ns,prec,tol", [
+    ("chain10_rbm", 512, "fp64", 1e-10),
+    ("chain10_rbm", 333, "fp32", 1e-4),
+    ("j1j2_6x6_ffnn", 300, "fp64", 1e-10),
+    ("j1j2_6x6_ffnn", 300, "fp32", 1e-4),
+    ("j1j2_6x6_ffnn", 300, "split_bf16", 1e-3),
+    ("j1j2_6x6_ffnn", 300, "split_bf16x3", 1e-6),
+    ("j1j2_10x10_ffnn5", 200, "split_bf16x3", 1e-6),
+])
+def test_sr_step(name, ns, prec, tol):
+    w = W.make_workload(name, ns)
+    model, theta, x, ham = dev_inputs(w)
+    dth, em, ev, nk = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec)
+    r = _oracle_all(w)
+    assert rel(dth.cpu().numpy(), r["dtheta"]) < tol
+    assert abs(em.cpu().numpy()[0] - r["e_mean"]) < max(tol, 1e-12) * abs(r["e_mean"])
+    assert np.array_equal(nk.cpu().numpy(), r["n_kept"])
+
+
+def test_single_sample_step_is_zero():
+    w = W.make_workload("chain10_rbm", 1)
+    model, theta, x, ham = dev_inputs(w)
+    dth, em, _, _ = nq().sr_step(model, theta, x, ham, w.block_off, 1e-4, 1e-10, 1.0, "fp64")
+    assert torch.all(dth == 0)
