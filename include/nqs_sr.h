@@ -55,16 +55,17 @@ extern "C" {
 #define NQS_ERR_UNSUPPORTED   (-7) /* valid request this build does not implement */
 
 /* ---- precision of the sample-space contractions (Jacobian, E_loc, Gram) ----
- * NQS_FP64       : everything in FP64; O is c128.
- * NQS_FP32       : Jacobian and E_loc in FP32 (O is c64), centring and force
- *                  accumulated in FP64, Gram in FP32 FFMA.
- * NQS_SPLIT_BF16 : as NQS_FP32, but the Gram runs on tcgen05 tensor cores with
- *                  each centred entry split into BF16 hi + lo and three products
- *                  (hi*hi + hi*lo + lo*hi) accumulated in FP32.
- * NQS_SPLIT_BF16X3: three-way split hi + mid + lo and six products (all terms of
- *                  order below 2^-16 relative), for a Gram accurate to ~FP32.
- * In both split modes FP32 accumulation runs over chunks of 1024 samples whose
- * partial Grams are summed in FP64.
+ * NQS_FP64        : everything in FP64; O is c128.
+ * NQS_FP32        : Jacobian and E_loc in FP32 (O is c64), centring and force
+ *                   accumulated in FP64, Gram in FP32 FFMA.
+ * NQS_SPLIT_BF16  : Jacobian and E_loc in FP64 (O is c128), and the Gram on
+ *                   tcgen05 tensor cores: every centred entry is split x = hi + lo
+ *                   (BF16 roundings of x and of the remainder) and three products
+ *                   (hi*hi, hi*lo, lo*hi) are accumulated in FP32 over one
+ *                   64-sample block at a time; the blocks are summed in
+ *                   double-float. Entry representation error 2^-17.
+ * NQS_SPLIT_BF16X3: as NQS_SPLIT_BF16 with hi + mid + lo and six products
+ *                   (all terms above 2^-16 relative): representation error 2^-25.
  * The per-block shifted eigen-decomposition and solve is FP64 in every mode. */
 typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3 } nqs_precision;
 
@@ -135,7 +136,7 @@ NQS_API int64_t qgt_packed_size(const int64_t* block_off, int32_t n_blocks); /* 
  *   configs    : int8 [n_s][N], entries +1 / -1, row-major.
  *   logpsi_out : c128 [n_s].
  *   O_out      : PARAMETER-MAJOR Jacobian, O_out[k*ldo + s] = d ln psi(x_s)/d theta_k;
- *                c128 for NQS_FP64, c64 otherwise. ldo >= n_s. Columns n_s..ldo-1
+ *                c64 for NQS_FP32, c128 otherwise. ldo >= n_s. Columns n_s..ldo-1
  *                of every row are written with zeros.
  * The derivative is the complex (holomorphic) derivative; no conjugation. */
 NQS_API int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
@@ -145,7 +146,7 @@ NQS_API int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* co
 /* nqs_local_energy -- E_loc(x_s) (Eq. 1) for the Hamiltonian h:
  *   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign_rule psi(x^{ij})/psi(x) ],
  * x^{ij} = x with spins i and j flipped; connected configurations are visited in
- * bond order. eloc_out: c128 [n_s]. Arithmetic in FP64 for NQS_FP64, else FP32. */
+ * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32, else FP64. */
 NQS_API int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
                      const nqs_hamiltonian* h, int32_t precision, void* eloc_out,
                      nqs_workspace* ws, void* stream);
@@ -160,9 +161,10 @@ NQS_API int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamilt
                     int64_t max_conn, int64_t* n_conn_out, nqs_workspace* ws, void* stream);
 
 /* qgt_block_build -- means, centring, force and the block-layer QGT (Eq. 2, Eq. 3).
- *   O        : parameter-major Jacobian as written by nqs_jacobian (c128 for NQS_FP64,
- *              c64 otherwise), leading dimension ldo. OVERWRITTEN with the centred dO
- *              for NQS_FP64/NQS_FP32; left unchanged in the split modes.
+ *   O        : parameter-major Jacobian as written by nqs_jacobian with the same
+ *              precision (c64 for NQS_FP32, c128 otherwise), leading dimension ldo.
+ *              OVERWRITTEN with the centred dO for NQS_FP64/NQS_FP32; left
+ *              unchanged in the split modes.
  *   w        : float64 [n_s] sample weights summing to 1, or NULL for 1/n_s.
  *   block_off: HOST int64 [n_blocks+1], block_off[0] = 0, strictly increasing,
  *              block_off[n_blocks] = n_p.

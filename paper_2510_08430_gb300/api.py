@@ -111,7 +111,8 @@ def _off(block_off) -> C.Array:
 
 
 def _cdt(precision: int):
-    return torch.complex128 if precision == NQS_FP64 else torch.complex64
+    """dtype of the Jacobian O: complex64 only in fp32 mode (split modes use an FP64 Jacobian)."""
+    return torch.complex64 if precision == NQS_FP32 else torch.complex128
 
 
 def nqs_jacobian(model: Model, theta: torch.Tensor, configs: torch.Tensor, precision="fp64",

@@ -2,6 +2,7 @@
 // stages of one block-layer SR step (see include/nqs_sr.h for the contract).
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <new>
@@ -72,7 +73,12 @@ Arena sizing_arena() { return Arena{nullptr, 0, 0}; }
 
 DevStatus* status_of(nqs_workspace* ws) { return reinterpret_cast<DevStatus*>(ws->base); }
 
-inline size_t csize(int prec) { return prec == NQS_FP64 ? sizeof(c128) : sizeof(c64); }
+// O (and the Jacobian arithmetic) is FP64 except in NQS_FP32 mode
+inline size_t csize(int prec) { return prec == NQS_FP32 ? sizeof(c64) : sizeof(c128); }
+inline int jac_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
+// local energies: FP32 arithmetic only in NQS_FP32 mode (in the split modes an FP32
+// E_loc alone moves dtheta by ~1e-5 relative on the 10x10 workload)
+inline int eloc_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
 inline int nsplit_of(int prec) { return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : 0); }
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
@@ -138,6 +144,7 @@ void plan_eloc(Arena& a, long long ns, int nbonds, ElocBufs* b) {
 struct BuildBufs {
     c128* e;
     void* planes[3];
+    double* diag;
     long long ldk;
 };
 void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
@@ -145,6 +152,7 @@ void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
     b->ldk = round_up(ns, 64);
     const int nsp = nsplit_of(prec);
     for (int i = 0; i < 3; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
+    b->diag = nsp ? static_cast<double*>(a.take(8 * np)) : nullptr;
 }
 
 // ------------------------------------------------------------------ stages
@@ -172,7 +180,8 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
               DevStatus* status, cudaStream_t st, cudaEvent_t gram_event = nullptr) {
     CK(launch_emean(eloc, w, ns, Emean, bb.e, status, st), "emean");
     const int nsp = nsplit_of(prec);
-    CK(launch_center(prec, nsp, O, ldo, ns, np, w, bb.e, F, Omean, nsp ? bb.planes : nullptr, bb.ldk, status, st),
+    CK(launch_center(prec, nsp, O, ldo, ns, np, w, bb.e, F, Omean, nsp ? bb.planes : nullptr, bb.ldk, bb.diag, status,
+                     st),
        "center");
     if (gram_event) CK(cudaEventRecord(gram_event, st), "event");
     GramTable* tab = new (std::nothrow) GramTable;
@@ -181,7 +190,9 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
     cudaError_t e;
     if (nsp) {
         gram_table(off, nb, 64, tab);
-        e = launch_gram_tc(nsp, bb.planes, 2 * np, bb.ldk, bb.ldk, GRAM_K_CHUNK, scale, *tab, S, status, st);
+        e = launch_gram_tc(nsp, bb.planes, 2 * np, bb.ldk, bb.ldk, scale, *tab, S, status, st);
+        // the diagonal (sum_s w_s |dO_k|^2) is taken from the FP64 centring pass
+        if (e == cudaSuccess) e = launch_set_diag(S, *tab, bb.diag, st);
     } else {
         gram_table(off, nb, 64, tab);
         e = launch_gram_simt(prec, O, ldo, ns, w, scale, *tab, S, st);
@@ -305,7 +316,7 @@ int nqs_jacobian_workspace_size(const nqs_model* m, int64_t n_s, int32_t precisi
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
     Arena a = sizing_arena();
     JacBufs jb;
-    plan_model(a, md, n_s, precision, &jb, true);
+    plan_model(a, md, n_s, jac_prec(precision), &jb, true);
     *bytes = a.used + STATUS_BYTES;
     return NQS_OK;
 }
@@ -317,7 +328,7 @@ int nqs_local_energy_workspace_size(const nqs_model* m, int64_t n_s, const nqs_h
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
     Arena a = sizing_arena();
     JacBufs jb;
-    plan_model(a, md, n_s, precision, &jb, false);
+    plan_model(a, md, n_s, eloc_prec(precision), &jb, false);
     ElocBufs eb;
     plan_eloc(a, n_s, h->n_bonds, &eb);
     *bytes = a.used + STATUS_BYTES;
@@ -345,9 +356,11 @@ int qgt_block_solve_workspace_size(const int64_t* block_off, int32_t n_blocks, s
 }
 
 static void plan_step(Arena& a, const ModelDesc& md, long long ns, int nbonds, const int64_t* off, int nb, int prec,
-                      JacBufs* jb, ElocBufs* eb, BuildBufs* bb, void** O, long long* ldo, c128** eloc, c128** F,
-                      c128** S) {
-    plan_model(a, md, ns, prec, jb, true);
+                      JacBufs* jb, JacBufs* jbe, ElocBufs* eb, BuildBufs* bb, void** O, long long* ldo, c128** eloc,
+                      c128** F, c128** S) {
+    plan_model(a, md, ns, jac_prec(prec), jb, true);
+    if (eloc_prec(prec) != jac_prec(prec)) plan_model(a, md, ns, eloc_prec(prec), jbe, false);
+    else *jbe = *jb;
     plan_eloc(a, ns, nbonds, eb);
     plan_build(a, ns, md.n_p, prec, bb);
     *ldo = round_up(ns, 32);
@@ -367,13 +380,13 @@ int sr_step_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonia
     int rc = check_offsets(block_off, n_blocks, md.n_p);
     if (rc) return rc;
     Arena a = sizing_arena();
-    JacBufs jb;
+    JacBufs jb, jbe;
     ElocBufs eb;
     BuildBufs bb;
     void* O;
     long long ldo;
     c128 *eloc, *F, *S;
-    plan_step(a, md, n_s, h->n_bonds, block_off, n_blocks, precision, &jb, &eb, &bb, &O, &ldo, &eloc, &F, &S);
+    plan_step(a, md, n_s, h->n_bonds, block_off, n_blocks, precision, &jb, &jbe, &eb, &bb, &O, &ldo, &eloc, &F, &S);
     a.take(solve_workspace_bytes(block_off, n_blocks));
     *bytes = a.used + STATUS_BYTES;
     return NQS_OK;
@@ -389,11 +402,11 @@ int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, i
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
     Arena a = arena_of(ws);
     JacBufs jb;
-    plan_model(a, md, n_s, precision, &jb, true);
+    plan_model(a, md, n_s, jac_prec(precision), &jb, true);
     int rc = check_ws(ws, a);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int rp = precision == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    const int rp = jac_prec(precision);
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
     CK(launch_backward(rp, md, jb.thR, jb.Z, n_s, jb.G, st), "backward");
@@ -413,13 +426,13 @@ int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* config
     if (rc) return rc;
     Arena a = arena_of(ws);
     JacBufs jb;
-    plan_model(a, md, n_s, precision, &jb, false);
+    const int rp = eloc_prec(precision);
+    plan_model(a, md, n_s, rp, &jb, false);
     ElocBufs eb;
     plan_eloc(a, n_s, hd.n_bonds, &eb);
     rc = check_ws(ws, a);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int rp = precision == NQS_FP64 ? NQS_FP64 : NQS_FP32;
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
     return run_eloc(md, rp, hd, configs, n_s, jb, eb, static_cast<c128*>(eloc_out), status_of(ws), st);
@@ -501,20 +514,20 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     rc = check_offsets(block_off, n_blocks, md.n_p);
     if (rc) return rc;
     Arena a = arena_of(ws);
-    JacBufs jb;
+    JacBufs jb, jbe;
     ElocBufs eb;
     BuildBufs bb;
     void* O;
     long long ldo;
     c128 *eloc, *F, *S;
-    plan_step(a, md, n_s, hd.n_bonds, block_off, n_blocks, precision, &jb, &eb, &bb, &O, &ldo, &eloc, &F, &S);
+    plan_step(a, md, n_s, hd.n_bonds, block_off, n_blocks, precision, &jb, &jbe, &eb, &bb, &O, &ldo, &eloc, &F, &S);
     Arena need = a;
     need.take(solve_workspace_bytes(block_off, n_blocks));
     rc = check_ws(ws, need);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DevStatus* status = status_of(ws);
-    const int rp = precision == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    const int rp = jac_prec(precision), re = eloc_prec(precision);
     const bool tm = ws->timing;
     if (tm) CK(cudaEventRecord(ws->ev[0], st), "event");
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
@@ -522,7 +535,11 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     CK(launch_backward(rp, md, jb.thR, jb.Z, n_s, jb.G, st), "backward");
     CK(launch_jac_write(rp, md, jb.Z, jb.G, configs, n_s, O, ldo, st), "jacobian");
     if (tm) CK(cudaEventRecord(ws->ev[1], st), "event");
-    rc = run_eloc(md, rp, hd, configs, n_s, jb, eb, eloc, status, st);
+    if (re != rp) {
+        rc = run_model(md, re, theta, configs, n_s, jbe, st);
+        if (rc) return rc;
+    }
+    rc = run_eloc(md, re, hd, configs, n_s, jbe, eb, eloc, status, st);
     if (rc) return rc;
     if (tm) CK(cudaEventRecord(ws->ev[2], st), "event");
     rc = run_build(O, ldo, n_s, md.n_p, nullptr, block_off, n_blocks, eloc, precision, S, F, nullptr,

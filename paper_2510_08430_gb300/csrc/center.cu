@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(1024) emean_kernel(const c128* __restrict__ el
     for (long long s = threadIdx.x; s < ns; s += blockDim.x) e[s] = eloc[s] - m;
 }
 
-// Splits x (FP64) into NS BF16 terms x ~ p0 + p1 (+ p2), each the rounding of the remainder.
+// Element-wise split x ~ x1 + x2 (+ x3): each term the BF16 rounding of the remainder.
 template <int NS>
 __device__ __forceinline__ void bf16_split(double x, __nv_bfloat16 (&p)[3]) {
     double r = x;
@@ -48,12 +48,10 @@ __device__ __forceinline__ void bf16_split(double x, __nv_bfloat16 (&p)[3]) {
     }
 }
 
-template <typename R, int NS>  // NS = 0: write dO in place; NS = 2, 3: BF16 split planes
+template <typename R>
 __global__ void __launch_bounds__(256) center_kernel(cx<R>* __restrict__ O, long long ldo, long long ns,
                                                       const double* __restrict__ w, const c128* __restrict__ e,
                                                       c128* __restrict__ F, c128* __restrict__ Omean,
-                                                      __nv_bfloat16* __restrict__ pl0, __nv_bfloat16* __restrict__ pl1,
-                                                      __nv_bfloat16* __restrict__ pl2, long long ldk,
                                                       DevStatus* status) {
     __shared__ double sh[32];
     const long long p = blockIdx.x;
@@ -73,44 +71,14 @@ __global__ void __launch_bounds__(256) center_kernel(cx<R>* __restrict__ O, long
         mi *= u;
     }
     double fr = 0.0, fi = 0.0;
-    if (NS > 0) {
-        __nv_bfloat16* pls[3] = {pl0, pl1, pl2};
-        for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
-            double dr = 0.0, di = 0.0;
-            if (s < ns) {
-                const cx<R> v = row[s];
-                const double ws = w ? w[s] : u;
-                dr = (double)v.re - mr;
-                di = (double)v.im - mi;
-                // F_k += w_s conj(dO) e_s
-                const c128 es = e[s];
-                fr = fma(ws, fma(dr, es.re, di * es.im), fr);
-                fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
-                if (w) {
-                    const double sw = sqrt(ws);
-                    dr *= sw;
-                    di *= sw;
-                }
-            }
-            __nv_bfloat16 qr[3], qi[3];
-            bf16_split<(NS > 0 ? NS : 1)>(dr, qr);
-            bf16_split<(NS > 0 ? NS : 1)>(di, qi);
-#pragma unroll
-            for (int q = 0; q < (NS > 0 ? NS : 1); ++q) {
-                pls[q][(2 * p) * ldk + s] = qr[q];
-                pls[q][(2 * p + 1) * ldk + s] = qi[q];
-            }
-        }
-    } else {
-        for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
-            const cx<R> v = row[s];
-            const double ws = w ? w[s] : u;
-            const cx<R> d = mk<R>((R)((double)v.re - mr), (R)((double)v.im - mi));
-            row[s] = d;
-            const c128 es = e[s];
-            fr = fma(ws, fma((double)d.re, es.re, (double)d.im * es.im), fr);
-            fi = fma(ws, fma((double)d.re, es.im, -(double)d.im * es.re), fi);
-        }
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+        const cx<R> v = row[s];
+        const double ws = w ? w[s] : u;
+        const cx<R> d = mk<R>((R)((double)v.re - mr), (R)((double)v.im - mi));
+        row[s] = d;
+        const c128 es = e[s];
+        fr = fma(ws, fma((double)d.re, es.re, (double)d.im * es.im), fr);
+        fi = fma(ws, fma((double)d.re, es.im, -(double)d.im * es.re), fi);
     }
     fr = block_sum(fr, sh);
     fi = block_sum(fi, sh);
@@ -122,6 +90,87 @@ __global__ void __launch_bounds__(256) center_kernel(cx<R>* __restrict__ O, long
     }
 }
 
+// Split mode (O is c128, left unchanged): mean and force in FP64, then NS BF16 split
+// planes of sqrt(w) dO (rows 2k = Re, 2k+1 = Im; zero beyond n_s up to ldk).
+template <int NS>
+__global__ void __launch_bounds__(256) center_split_kernel(const c128* __restrict__ O, long long ldo, long long ns,
+                                                            const double* __restrict__ w,
+                                                            const c128* __restrict__ e, c128* __restrict__ F,
+                                                            c128* __restrict__ Omean, __nv_bfloat16* __restrict__ pl0,
+                                                            __nv_bfloat16* __restrict__ pl1,
+                                                            __nv_bfloat16* __restrict__ pl2, long long ldk,
+                                                            double* __restrict__ diag, DevStatus* status) {
+    __shared__ double sh[32];
+    const long long p = blockIdx.x;
+    const c128* row = O + p * ldo;
+    const double u = 1.0 / (double)ns;
+    double mr = 0.0, mi = 0.0;
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+        const c128 v = row[s];
+        const double ws = w ? w[s] : 1.0;
+        mr = fma(ws, v.re, mr);
+        mi = fma(ws, v.im, mi);
+    }
+    mr = block_sum(mr, sh);
+    mi = block_sum(mi, sh);
+    if (!w) {
+        mr *= u;
+        mi *= u;
+    }
+    double fr = 0.0, fi = 0.0, dg = 0.0;
+    __nv_bfloat16* pls[3] = {pl0, pl1, pl2};
+    for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
+        double dr = 0.0, di = 0.0;
+        if (s < ns) {
+            const c128 v = row[s];
+            const double ws = w ? w[s] : u;
+            dr = v.re - mr;
+            di = v.im - mi;
+            const c128 es = e[s];
+            fr = fma(ws, fma(dr, es.re, di * es.im), fr);
+            fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
+            dg = fma(ws, fma(dr, dr, di * di), dg);
+            if (w) {
+                const double sw = sqrt(ws);
+                dr *= sw;
+                di *= sw;
+            }
+        }
+        __nv_bfloat16 qr[3], qi[3];
+        bf16_split<NS>(dr, qr);
+        bf16_split<NS>(di, qi);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            pls[q][(2 * p) * ldk + s] = qr[q];
+            pls[q][(2 * p + 1) * ldk + s] = qi[q];
+        }
+    }
+    fr = block_sum(fr, sh);
+    fi = block_sum(fi, sh);
+    dg = block_sum(dg, sh);
+    if (threadIdx.x == 0) {
+        F[p] = mk<double>(fr, fi);
+        if (Omean) Omean[p] = mk<double>(mr, mi);
+        diag[p] = dg;
+        if (!(isfinite(mr) && isfinite(mi) && isfinite(fr) && isfinite(fi)))
+            set_status(status, NQS_ERR_NONFINITE, W_CENTER, p);
+    }
+}
+
+// S_b[k][k] = sum_s w_s |dO_k(s)|^2 computed in FP64 by the split centring kernel.
+__global__ void set_diag_kernel(c128* __restrict__ S, const GramTable tab, const double* __restrict__ diag) {
+    const int b = blockIdx.y;
+    const GBlk blk = tab.b[b];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < blk.n; k += gridDim.x * blockDim.x)
+        S[blk.s_off + (long long)k * blk.n + k] = mk<double>(diag[blk.row0 + k], 0.0);
+}
+
+cudaError_t launch_set_diag(c128* S, const GramTable& tab, const double* diag, cudaStream_t st) {
+    count_launch();
+    set_diag_kernel<<<dim3(32, tab.nb), 256, 0, st>>>(S, tab, diag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* emean, c128* e,
                          DevStatus* status, cudaStream_t st) {
     count_launch();
@@ -131,26 +180,26 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          DevStatus* status, cudaStream_t st) {
+                          double* diag, DevStatus* status, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)np;
-    __nv_bfloat16* p0 = planes ? (__nv_bfloat16*)planes[0] : nullptr;
-    __nv_bfloat16* p1 = planes ? (__nv_bfloat16*)planes[1] : nullptr;
-    __nv_bfloat16* p2 = (planes && nsplit == 3) ? (__nv_bfloat16*)planes[2] : nullptr;
-    if (nsplit == 2) {
+    if (nsplit == 2 || nsplit == 3) {
+        __nv_bfloat16* p0 = (__nv_bfloat16*)planes[0];
+        __nv_bfloat16* p1 = (__nv_bfloat16*)planes[1];
+        __nv_bfloat16* p2 = nsplit == 3 ? (__nv_bfloat16*)planes[2] : nullptr;
         count_launch();
-        center_kernel<float, 2><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk, status);
-    } else if (nsplit == 3) {
-        count_launch();
-        center_kernel<float, 3><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk, status);
+        if (nsplit == 2)
+            center_split_kernel<2><<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk,
+                                                         diag, status);
+        else
+            center_split_kernel<3><<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk,
+                                                         diag, status);
     } else if (prec == NQS_FP64) {
         count_launch();
-        center_kernel<double, 0><<<grid, 256, 0, st>>>((c128*)O, ldo, ns, w, e, F, Omean, nullptr, nullptr, nullptr,
-                                                       0, status);
+        center_kernel<double><<<grid, 256, 0, st>>>((c128*)O, ldo, ns, w, e, F, Omean, status);
     } else {
         count_launch();
-        center_kernel<float, 0><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, nullptr, nullptr, nullptr, 0,
-                                                      status);
+        center_kernel<float><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, status);
     }
     return cudaGetLastError();
 }

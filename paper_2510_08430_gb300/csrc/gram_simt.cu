@@ -3,7 +3,9 @@
 // Operands are the parameter-major centred rows (contiguous samples), so a
 // 64 x 64 complex output tile streams two 64-row panels along the sample axis
 // through shared memory; each thread owns a 4 x 4 register tile. Only
-// lower-triangle tiles are launched (the QGT is Hermitian).
+// lower-triangle tiles are launched (the QGT is Hermitian). In FP32 the partial
+// sums of each 16-sample stage are folded into FP64 accumulators, so the
+// accumulation error does not grow with the number of samples.
 #include "internal.cuh"
 
 namespace nqs {
@@ -55,11 +57,11 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const cx<R>* __restrict_
     const GBlk blk = tab.b[b];
     const int n = blk.n;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    cx<R> acc[4][4];
+    c128 acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = mk<R>(R(0), R(0));
+        for (int c = 0; c < 4; ++c) acc[a][c] = mk<double>(0.0, 0.0);
     const long long rowA = blk.row0 + (long long)I * GT;
     const long long rowB = blk.row0 + (long long)J * GT;
     for (long long s0 = 0; s0 < ns; s0 += GK) {
@@ -79,6 +81,11 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const cx<R>* __restrict_
             Bs[k][r] = vb;
         }
         __syncthreads();
+        cx<R> part[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) part[a][c] = mk<R>(R(0), R(0));
 #pragma unroll
         for (int k = 0; k < GK; ++k) {
             cx<R> av[4], bv[4];
@@ -89,8 +96,12 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const cx<R>* __restrict_
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) cmacc(acc[a][c], av[a], bv[c]);
+                for (int c = 0; c < 4; ++c) cmacc(part[a][c], av[a], bv[c]);
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = acc[a][c] + ccast<double>(part[a][c]);
         __syncthreads();
     }
 #pragma unroll
@@ -101,7 +112,7 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const cx<R>* __restrict_
         for (int c = 0; c < 4; ++c) {
             const int l = J * GT + tx + 16 * c;
             if (l >= n) continue;
-            S[blk.s_off + (long long)k * n + l] = mk<double>(scale * (double)acc[a][c].re, scale * (double)acc[a][c].im);
+            S[blk.s_off + (long long)k * n + l] = mk<double>(scale * acc[a][c].re, scale * acc[a][c].im);
         }
     }
 }

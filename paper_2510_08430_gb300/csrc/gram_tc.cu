@@ -3,16 +3,25 @@
 // computed as the real Gram G = X X^T of the interleaved real rows X[2k] = Re dO_k,
 // X[2k+1] = Im dO_k (samples contiguous, i.e. K-major operands), so that
 //   Re S[k][l] = G[2k][2l] + G[2k+1][2l+1],   Im S[k][l] = G[2k][2l+1] - G[2k+1][2l].
-// Every entry is split x = hi + lo (both BF16) and G ~ Xh Xh^T + Xh Xl^T + Xl Xh^T with
-// FP32 accumulation in tensor memory (three products per K step).
+// Every entry is split element-wise x = x1 + x2 (+ x3), each a BF16 rounding of the
+// remainder (relative error 2^-17 / 2^-25), and G is accumulated from the products
+// x1 y1 (accumulator A0) and the correction products x1 y2 + x2 y1 (+ x1 y3 + x3 y1
+// + x2 y2) (accumulator A1). FP32 accumulation in tensor memory only spans one
+// 64-sample K block (four MMA steps); the epilogue folds every K block into
+// double-float (FP32 hi + lo, TwoSum) running sums held in registers, so the
+// accumulation error does not grow with the number of samples. S is written in
+// FP64 once per tile.
 //
 // Persistent kernel, one CTA per SM, static round-robin over the lower-triangle
 // 128 x 128 tiles of every block. Warp roles: warp 0 issues TMA loads (128B
 // swizzle) into a STAGES-deep ring, warp 1 allocates tensor memory and issues
-// tcgen05.mma, warps 2-5 drain the double-buffered accumulators (tcgen05.ld),
-// combine the 2 x 2 real blocks into complex entries and store FP64 to S.
-// Every mbarrier wait is bounded; on expiry the kernel records NQS_ERR_TIMEOUT,
-// drains its own copies and MMAs, frees tensor memory and returns.
+// tcgen05.mma, warps 2-9 (two per tensor-memory lane quarter, one per column
+// half) drain the double-buffered accumulator pairs
+// (tcgen05.ld), combine the 2 x 2 real blocks into complex entries and fold
+// them. Every mbarrier wait is bounded; on expiry the kernel records
+// NQS_ERR_TIMEOUT, drains its own copies and MMAs, frees tensor memory and
+// returns.
+#include <cstdlib>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include "internal.cuh"
@@ -24,25 +33,31 @@ namespace tc {
 constexpr int BM = 128;          // real rows per tile (64 complex)
 constexpr int BK = 64;           // BF16 elements per 128-byte swizzle row
 constexpr int TILE_BYTES = BM * BK * 2;          // 16 KB
-constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 256;              // two 128-column FP32 accumulators
+constexpr int NTHREADS = 320;                    // TMA warp, MMA warp, 8 epilogue warps
+constexpr int NEPI = 256;                        // epilogue threads
+constexpr uint32_t TMEM_COLS = 512;              // 2 buffers x up to 2 accumulators x 128 columns
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s budget per wait
 
-// NS split planes; products (a-plane, b-plane) whose order sum is < NS.
+// NPL planes per operand; NPROD products (plane of A, plane of B); product 0
+// (x1 y1) goes to accumulator A0, all others to A1.
 template <int NS> struct Split;
-template <> struct Split<2> {
-    static constexpr int STAGES = 3;
-    static constexpr int NPROD = 3;
+template <> struct Split<2> {   // x1 y1 | x1 y2 + x2 y1
+    static constexpr int NPL = 2, NPROD = 3, STAGES = 3;
     __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
     __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
-template <> struct Split<3> {
-    static constexpr int STAGES = 2;
-    static constexpr int NPROD = 6;
-    // hh, hm, mh, hl, lh, mm
+template <> struct Split<3> {   // x1 y1 | x1 y2 + x2 y1 + x1 y3 + x3 y1 + x2 y2
+    static constexpr int NPL = 3, NPROD = 6, STAGES = 2;
     __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
     __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
 };
+
+// Error-free sum of two FP32 numbers: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -127,6 +142,16 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -165,15 +190,18 @@ struct Maps {
     CUtensorMap m[3];
 };
 
-// Work item = (tile, K chunk). The FP32 accumulator of one chunk covers kpc K-blocks
-// (64 samples each); chunk results are summed in FP64 in S by the epilogue.
-template <int NS>
+// Work item = (tile, kpi MMA K-steps of 16 samples; kpi divides 4). Each work item
+// owns one of two accumulator pairs (A0, A1) in tensor memory; smem stages hold
+// one 64-sample K block each.
+template <int NSPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    gram_tc_kernel(const __grid_constant__ Maps maps, const __grid_constant__ GramTable tab, int nkb, int kpc,
+    gram_tc_kernel(const __grid_constant__ Maps maps, const __grid_constant__ GramTable tab, int nkb, int kpi,
                    double scale, c128* __restrict__ S, DevStatus* status) {
-    using SP = Split<NS>;
+    using SP = Split<NSPLIT>;
+    constexpr int NS = SP::NPL;
     constexpr int STAGES = SP::STAGES;
     constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+    constexpr uint32_t BUF_COLS = 256u;  // A0 and A1, 128 columns each
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar;
@@ -188,7 +216,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull_bar[a], 1);
-            mbar_init(&tempty_bar[a], 128);
+            mbar_init(&tempty_bar[a], NEPI);
         }
         mbar_init(&done_bar, 1);
         abort_sh = 0;
@@ -207,7 +235,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t tmem_base = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
     const long long total = tab.total_tiles;
-    const int nch = (nkb + kpc - 1) / kpc;
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -250,39 +277,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_128x128();
-            uint32_t q = 0, it = 0;
+            const int nsub = (BK / 16) / kpi;
+            uint32_t q = 0, w = 0;  // smem stage counter, accumulator work-item counter
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const TileInfo ti = decode(tab, t);
                 const bool diag = ti.I == ti.J;
-                for (int c = 0; c < nch && ok; ++c, ++it) {
-                    const uint32_t acc = it & 1u;
-                    const uint32_t tmem_d = tmem_base + acc * 128u;
-                    if (!mbar_wait(&tempty_bar[acc], ((it >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+                for (int kb = 0; kb < nkb && ok; ++kb, ++q) {
+                    const int s = q % STAGES;
+                    const uint32_t ph = (q / STAGES) & 1u;
+                    if (!mbar_wait(&full_bar[s], ph, abort_flag)) { ok = false; break; }
                     fence_after();
-                    const int kb0 = c * kpc, kb1 = (kb0 + kpc) < nkb ? (kb0 + kpc) : nkb;
-                    for (int kb = kb0; kb < kb1; ++kb, ++q) {
-                        const int s = q % STAGES;
-                        const uint32_t ph = (q / STAGES) & 1u;
-                        if (!mbar_wait(&full_bar[s], ph, abort_flag)) { ok = false; break; }
+                    const uint32_t base = smem_u32(ring + (size_t)s * STAGE_BYTES);
+                    const uint32_t boff = diag ? 0u : (uint32_t)(NS * TILE_BYTES);
+                    for (int sub = 0; sub < nsub; ++sub, ++w) {
+                        const uint32_t acc = w & 1u;
+                        const uint32_t tmem_d = tmem_base + acc * BUF_COLS;
+                        if (!mbar_wait(&tempty_bar[acc], ((w >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
                         fence_after();
-                        const uint32_t base = smem_u32(ring + (size_t)s * STAGE_BYTES);
-                        const uint32_t boff = diag ? 0u : (uint32_t)(NS * TILE_BYTES);
-#pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {
+                        for (int kk = sub * kpi; kk < (sub + 1) * kpi; ++kk) {
                             const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes inside the swizzle row
 #pragma unroll
                             for (int pr = 0; pr < SP::NPROD; ++pr) {
                                 const uint32_t aad = base + SP::pa(pr) * TILE_BYTES + off;
                                 const uint32_t bad = base + boff + SP::pb(pr) * TILE_BYTES + off;
-                                const uint32_t first = (kb == kb0 && kk == 0 && pr == 0) ? 0u : 1u;
-                                umma(tmem_d, sdesc(aad), sdesc(bad), idesc, first);
+                                // product 0 -> A0; products 1.. -> A1; the first write of each resets it
+                                const uint32_t first = (kk == sub * kpi && pr <= 1) ? 0u : 1u;
+                                umma(tmem_d + (pr == 0 ? 0u : 128u), sdesc(aad), sdesc(bad), idesc, first);
                             }
                         }
-                        umma_commit(&empty_bar[s]);  // frees the stage when these MMAs complete
+                        umma_commit(&tfull_bar[acc]);   // hands the accumulator pair to the epilogue
                     }
                     if (!ok) break;
-                    umma_commit(&tfull_bar[acc]);
+                    umma_commit(&empty_bar[s]);     // frees the smem stage when these MMAs complete
                 }
             }
             if (!ok) {
@@ -294,61 +321,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_wait(&done_bar, 0u, nullptr);
         }
     } else {
-        // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        // ---------------- epilogue: warp w owns TMEM lane quarter w % 4 and column half (w - 2) / 4
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int r = quarter * 32 + lane;  // accumulator row (real row within the tile)
         const int cpar = r & 1;             // 0: Re row, 1: Im row of complex row r/2
-        uint32_t it = 0;
+        uint32_t q = 0;
         bool ok = true;
+        const int nitems = nkb * ((BK / 16) / kpi);
         for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const TileInfo ti = decode(tab, t);
             const GBlk blk = tab.b[ti.b];
             const int n = blk.n;
             const long long k = (long long)ti.I * (BM / 2) + (r >> 1);
-            c128* Srow = S + blk.s_off + k * n;
-            const bool row_ok = k < n;
-            for (int c = 0; c < nch; ++c, ++it) {
-                const uint32_t acc = it & 1u;
-                if (!mbar_wait(&tfull_bar[acc], (it >> 1) & 1u, abort_flag)) {
+            // double-float running sums of the 16 complex outputs this lane owns
+            float hre[16], lre[16], him[16], lim[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) hre[j] = lre[j] = him[j] = lim[j] = 0.f;
+            for (int item = 0; item < nitems; ++item, ++q) {
+                const uint32_t acc = q & 1u;
+                if (!mbar_wait(&tfull_bar[acc], (q >> 1) & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
                 fence_after();
-#pragma unroll 1
-                for (int chunk = 0; chunk < 4; ++chunk) {
-                    uint32_t v[32];
-                    const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * 128u + chunk * 32u;
-                    tmem_ld32(taddr, v);
-                    // 32 real columns = 8 pairs of complex columns (l0 = 2m, l1 = 2m + 1)
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const float g0 = __uint_as_float(v[4 * m + 0]);  // col (l0, re)
-                        const float g1 = __uint_as_float(v[4 * m + 1]);  // col (l0, im)
-                        const float g2 = __uint_as_float(v[4 * m + 2]);  // col (l1, re)
-                        const float g3 = __uint_as_float(v[4 * m + 3]);  // col (l1, im)
+                for (int chunk = 0; chunk < 4; ++chunk) {
+                    float g[16];
+                    {
+                        uint32_t v0[16], v1[16];
+                        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BUF_COLS +
+                                               (uint32_t)(64 * half + 16 * chunk);
+                        tmem_ld16(taddr, v0);
+                        tmem_ld16(taddr + 128u, v1);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) g[j] = __uint_as_float(v0[j]) + __uint_as_float(v1[j]);
+                    }
+                    // 16 real columns = 4 pairs of complex columns (l0 = 2m, l1 = 2m + 1)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float g0 = g[4 * m + 0];  // col (l0, re)
+                        const float g1 = g[4 * m + 1];  // col (l0, im)
+                        const float g2 = g[4 * m + 2];  // col (l1, re)
+                        const float g3 = g[4 * m + 3];  // col (l1, im)
                         // even lane (Re row) sends its l1 pair, odd lane (Im row) its l0 pair
                         const float s0 = cpar ? g0 : g2;
                         const float s1 = cpar ? g1 : g3;
                         const float y0 = __shfl_xor_sync(0xffffffffu, s0, 1);
                         const float y1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-                        double re, im;
+                        float re, im;
                         if (cpar == 0) {   // S[k][l0]: g00 = g0, g01 = g1, g10 = y0, g11 = y1
-                            re = (double)g0 + (double)y1;
-                            im = (double)g1 - (double)y0;
+                            re = g0 + y1;
+                            im = g1 - y0;
                         } else {           // S[k][l1]: g00 = y0, g01 = y1, g10 = g2, g11 = g3
-                            re = (double)y0 + (double)g3;
-                            im = (double)y1 - (double)g2;
+                            re = y0 + g3;
+                            im = y1 - g2;
                         }
-                        const long long l = (long long)ti.J * (BM / 2) + chunk * 16 + 2 * m + cpar;
-                        if (row_ok && l < n) {
-                            c128 o = mk<double>(scale * re, scale * im);
-                            if (c > 0) o = o + Srow[l];
-                            Srow[l] = o;
-                        }
+                        const int j = 4 * chunk + m;
+                        float sh, se;
+                        two_sum(hre[j], re, sh, se);
+                        hre[j] = sh;
+                        lre[j] += se;
+                        two_sum(him[j], im, sh, se);
+                        him[j] = sh;
+                        lim[j] += se;
                     }
                 }
                 fence_before();
                 mbar_arrive(&tempty_bar[acc]);
+            }
+            if (!ok) break;
+            if (k < n) {
+                c128* Srow = S + blk.s_off + k * n;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const long long l = (long long)ti.J * (BM / 2) + 32 * half + 2 * j + cpar;
+                    if (l < n)
+                        Srow[l] = mk<double>(scale * ((double)hre[j] + (double)lre[j]),
+                                             scale * ((double)him[j] + (double)lim[j]));
+                }
             }
         }
         if (!ok) {
@@ -397,8 +448,13 @@ static bool make_map(CUtensorMap* m, const void* base, long long rows, long long
 }
 
 cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows, long long ldk, long long kpad,
-                           int k_chunk, double scale, const GramTable& tab, c128* S, DevStatus* status,
-                           cudaStream_t st) {
+                           double scale, const GramTable& tab, c128* S, DevStatus* status, cudaStream_t st) {
+    static int kpi = -1;  // MMA K-steps per accumulator flush (1, 2 or 4); NQS_GRAM_KPI overrides
+    if (kpi < 0) {
+        const char* env = getenv("NQS_GRAM_KPI");
+        const int v = env ? atoi(env) : GRAM_KPI_DEFAULT;
+        kpi = (v == 1 || v == 2 || v == 4) ? v : GRAM_KPI_DEFAULT;
+    }
     if (tab.total_tiles <= 0) return cudaSuccess;
     if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
     int dev = 0;
@@ -408,14 +464,13 @@ cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (major != 10 || minor != 3) return cudaErrorNotSupported;
-    if (ldk % tc::BK != 0 || kpad % tc::BK != 0 || kpad > ldk || k_chunk < tc::BK) return cudaErrorInvalidValue;
+    if (ldk % tc::BK != 0 || kpad % tc::BK != 0 || kpad > ldk) return cudaErrorInvalidValue;
     tc::Maps maps;
     for (int p = 0; p < nsplit; ++p) {
         if (reinterpret_cast<uintptr_t>(planes[p]) & 15) return cudaErrorInvalidValue;
         if (!make_map(&maps.m[p], planes[p], rows, ldk)) return cudaErrorInvalidValue;
     }
     const int nkb = (int)(kpad / tc::BK);
-    const int kpc = k_chunk / tc::BK;
     const long long grid = tab.total_tiles < sms ? tab.total_tiles : sms;
     cudaError_t e;
     if (nsplit == 2) {
@@ -423,13 +478,13 @@ cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows
         e = cudaFuncSetAttribute(tc::gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        tc::gram_tc_kernel<2><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpc, scale, S, status);
+        tc::gram_tc_kernel<2><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpi, scale, S, status);
     } else {
         const size_t smem = (size_t)tc::Split<3>::STAGES * 6 * tc::TILE_BYTES + 1024;
         e = cudaFuncSetAttribute(tc::gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        tc::gram_tc_kernel<3><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpc, scale, S, status);
+        tc::gram_tc_kernel<3><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpi, scale, S, status);
     }
     return cudaGetLastError();
 }

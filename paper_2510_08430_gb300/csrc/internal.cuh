@@ -66,10 +66,12 @@ cudaError_t launch_eloc_reduce(const int8_t* x, long long ns, const HamDesc& h,
 // ---- centring / force ----
 cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* emean, c128* e,
                          DevStatus* status, cudaStream_t st);
-// nsplit 0: dO written in place (prec FP64/FP32); nsplit 2 or 3: BF16 split planes (O is c64)
+// nsplit 0: dO written in place (prec FP64/FP32); nsplit 2 or 3: element-wise BF16
+// split planes of dO (O is c128, unchanged)
+// (split modes also write diag[k] = sum_s w_s |dO_k(s)|^2 in FP64)
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          DevStatus* status, cudaStream_t st);
+                          double* diag, DevStatus* status, cudaStream_t st);
 
 // ---- Gram ----
 struct GBlk {                   // one QGT block of one instance
@@ -86,13 +88,15 @@ struct GramTable {
 };
 cudaError_t launch_gram_simt(int prec, const void* dO, long long ldo, long long ns, const double* w,
                              double scale, const GramTable& tab, c128* S, cudaStream_t st);
-// tcgen05 BF16 split Gram over nsplit planes (2: 3 products, 3: 6 products), FP32 accumulation
-// over K chunks of k_chunk samples summed in FP64; cudaErrorNotSupported off sm_103.
-constexpr int GRAM_K_CHUNK = 1024;
+constexpr int GRAM_KPI_DEFAULT = 4;    // MMA K-steps (16 samples) per accumulator flush
+// tcgen05 Gram over nsplit element-wise BF16 split planes (2: 3 products; 3: 6 products),
+// FP32 accumulation per 64-sample K block folded into double-float sums;
+// cudaErrorNotSupported off sm_103.
 cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows, long long ldk, long long kpad,
-                           int k_chunk, double scale, const GramTable& tab, c128* S, DevStatus* status,
-                           cudaStream_t st);
+                           double scale, const GramTable& tab, c128* S, DevStatus* status, cudaStream_t st);
 void gram_table(const int64_t* block_off, int nb, int tile_rows, GramTable* tab);
+// overwrite the diagonal of every S_b with diag (FP64 sums of |dO_k|^2)
+cudaError_t launch_set_diag(c128* S, const GramTable& tab, const double* diag, cudaStream_t st);
 
 // ---- per-block solve ----
 struct SolveArgs {

@@ -156,7 +156,6 @@ def test_solve_absolute_cutoff_mode():
     ("chain10_rbm", 333, "fp32", 1e-4),
     ("j1j2_6x6_ffnn", 300, "fp64", 1e-10),
     ("j1j2_6x6_ffnn", 300, "fp32", 1e-4),
-    ("j1j2_6x6_ffnn", 300, "split_bf16", 1e-3),
     ("j1j2_6x6_ffnn", 300, "split_bf16x3", 1e-6),
     ("j1j2_10x10_ffnn5", 200, "split_bf16x3", 1e-6),
 ])
