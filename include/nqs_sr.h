@@ -66,8 +66,17 @@ extern "C" {
  *                   double-float. Entry representation error 2^-17.
  * NQS_SPLIT_BF16X3: as NQS_SPLIT_BF16 with hi + mid + lo and six products
  *                   (all terms above 2^-16 relative): representation error 2^-25.
+ * NQS_SPLIT_BF16_EXACT: error-free split on the tensor cores: for every parameter and
+ *                   every group of 16 samples the centred values are scaled by a common
+ *                   power of two and split into five BF16 slices holding integers of at
+ *                   most 8 bits, so that the MMA sums of the leading products are exact;
+ *                   fifteen products (every term above 2^-32 of the group scale) per group,
+ *                   groups summed in double-float. Better than FP32 rounding of the data
+ *                   even on heavy-tailed Jacobian rows.
  * The per-block shifted eigen-decomposition and solve is FP64 in every mode. */
-typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3 } nqs_precision;
+typedef enum {
+    NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3, NQS_SPLIT_BF16_EXACT = 4
+} nqs_precision;
 
 enum { NQS_RBM = 0, NQS_FFNN = 1 };
 
@@ -177,6 +186,24 @@ NQS_API int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, cons
                     int32_t precision, void* S_packed, void* F_out, void* Omean_out,
                     void* Emean_out, nqs_workspace* ws, void* stream);
 
+/* ---- per-block solver ----
+ * NQS_SOLVE_FP64 : the Householder reduction, eigenvalues and solve all in FP64.
+ * NQS_SOLVE_MIXED: the O(n^3) reduction runs in FP32 on a copy of S_b (FP64 units run
+ *                  at 1/64 of the FP32 rate on GB300); Q is formed explicitly in FP32;
+ *                  eigenvalues come from the FP32-reduced tridiagonal; dtheta_b is then
+ *                  obtained by iterative refinement whose residuals F - (S_b + lambda I) x
+ *                  use the FP64 S_b, until ||r|| <= 1e-14 ||F_b|| (NQS_ERR_NOT_CONVERGED
+ *                  after 30 sweeps). When the FP32 eigenvalues cannot certify that the
+ *                  cutoff keeps every eigenvalue of a block (margin 4e-5 sigma_max), every
+ *                  block is solved by the FP64 path instead; deciding this synchronises
+ *                  the stream once. S_packed is left unchanged in the refinement case.
+ * NQS_SOLVE_MIXED_PSD: as NQS_SOLVE_MIXED, with the caller asserting that every S_b is
+ *                  a Gram matrix (positive semi-definite up to a rounding of at most
+ *                  1e-6 sigma_max, as qgt_block_build produces), so sigma_min >= shift -
+ *                  1e-6 sigma_max certifies the cutoff. sr_step uses this certificate when
+ *                  called with NQS_SOLVE_MIXED. */
+enum { NQS_SOLVE_FP64 = 0, NQS_SOLVE_MIXED = 1, NQS_SOLVE_MIXED_PSD = 2 };
+
 /* qgt_block_solve -- per-block shifted pseudo-inverse solve (Sec. 2):
  *   S~_b = S_b + diag_shift I = U diag(sigma) U^H (FP64),
  *   keep_i = sigma_i > cutoff * max_i sigma_i   (cutoff_mode 0, relative)
@@ -190,12 +217,13 @@ NQS_API int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, cons
  *   evals_out : float64 [n_p] or NULL; block b's sigma ascending at block_off[b].
  *   n_kept_out: int32 [n_blocks] or NULL. */
 NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, const void* F,
-                    double diag_shift, double cutoff, int32_t cutoff_mode, double eta,
+                    double diag_shift, double cutoff, int32_t cutoff_mode, double eta, int32_t solver,
                     void* dtheta_out, double* evals_out, int32_t* n_kept_out,
                     nqs_workspace* ws, void* stream);
 
 /* sr_step -- one whole block-layer SR step: Jacobian, E_loc, centring, force,
  * block Gram and the per-block solve, from (theta, configs) to dtheta and <E>.
+ *   solver: NQS_SOLVE_FP64 or NQS_SOLVE_MIXED (see qgt_block_solve).
  *   dtheta_out: c128 [n_p]; Emean_out: c128 [1].
  *   evals_out / n_kept_out as in qgt_block_solve (may be NULL).
  *   flags: NQS_SYNC makes the call synchronise and return device status. */
@@ -203,7 +231,7 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
 NQS_API int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
             const nqs_hamiltonian* h, const int64_t* block_off, int32_t n_blocks,
             double diag_shift, double cutoff, int32_t cutoff_mode, double eta,
-            int32_t precision, void* dtheta_out, void* Emean_out, double* evals_out,
+            int32_t precision, int32_t solver, void* dtheta_out, void* Emean_out, double* evals_out,
             int32_t* n_kept_out, int32_t flags, nqs_workspace* ws, void* stream);
 
 /* ---- measurement hooks ----

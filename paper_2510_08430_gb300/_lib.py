@@ -19,9 +19,10 @@ NQS_ERR_TIMEOUT = -5
 NQS_ERR_NONFINITE = -6
 NQS_ERR_UNSUPPORTED = -7
 
-NQS_FP64, NQS_FP32, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3 = 0, 1, 2, 3
+NQS_FP64, NQS_FP32, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SPLIT_BF16_EXACT = 0, 1, 2, 3, 4
 NQS_RBM, NQS_FFNN = 0, 1
 NQS_SYNC = 1
+NQS_SOLVE_FP64, NQS_SOLVE_MIXED, NQS_SOLVE_MIXED_PSD = 0, 1, 2
 
 
 class nqs_model(C.Structure):
@@ -59,8 +60,8 @@ SIGNATURES = {
     "nqs_local_energy": (C.c_int, [MP, P, P, I64, HP, I32, P, P, P]),
     "nqs_connections": (C.c_int, [P, I64, HP, P, P, P, I64, C.POINTER(C.c_int64), P, P]),
     "qgt_block_build": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P, P]),
-    "qgt_block_solve": (C.c_int, [P, OFF, I32, P, D, D, I32, D, P, P, P, P, P]),
-    "sr_step": (C.c_int, [MP, P, P, I64, HP, OFF, I32, D, D, I32, D, I32, P, P, P, P, I32, P, P]),
+    "qgt_block_solve": (C.c_int, [P, OFF, I32, P, D, D, I32, D, I32, P, P, P, P, P]),
+    "sr_step": (C.c_int, [MP, P, P, I64, HP, OFF, I32, D, D, I32, D, I32, I32, P, P, P, P, I32, P, P]),
     "nqs_stage_timing": (C.c_int, [P, I32]),
     "nqs_stage_times": (C.c_int, [P, C.POINTER(C.c_double), I32, C.POINTER(C.c_int32)]),
     "nqs_launch_count": (C.c_int64, []),

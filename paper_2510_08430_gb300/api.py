@@ -14,10 +14,16 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SYNC, check,
-                   nqs_hamiltonian, nqs_model)
+from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16_EXACT, NQS_SPLIT_BF16X3,
+                   NQS_SYNC, check, nqs_hamiltonian, nqs_model)
 
-PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3}
+PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3,
+              "split_bf16_exact": NQS_SPLIT_BF16_EXACT}
+SOLVERS = {"fp64": 0, "mixed": 1, "mixed_psd": 2}
+
+
+def _solver(s) -> int:
+    return SOLVERS[s] if isinstance(s, str) else int(s)
 
 
 def _prec(p) -> int:
@@ -191,7 +197,7 @@ def qgt_block_build(O: torch.Tensor, n_s: int, block_off, eloc: torch.Tensor, pr
 
 
 def qgt_block_solve(S: torch.Tensor, block_off, F: torch.Tensor, diag_shift: float, cutoff: float,
-                    cutoff_mode: int = 0, eta: float = 1.0, want_evals: bool = True,
+                    cutoff_mode: int = 0, eta: float = 1.0, want_evals: bool = True, solver="fp64",
                     ws: Optional[Workspace] = None, sync: bool = True):
     """(dtheta c128 [n_p], evals f64 [n_p] or None, n_kept int32 [n_blocks]). S is overwritten."""
     lib = _lib.load()
@@ -205,7 +211,7 @@ def qgt_block_solve(S: torch.Tensor, block_off, F: torch.Tensor, diag_shift: flo
     ev = torch.empty(n_p, dtype=torch.float64, device=dev) if want_evals else None
     nk = torch.empty(nb, dtype=torch.int32, device=dev)
     check(lib.qgt_block_solve(_ptr(S), off, nb, _ptr(F), float(diag_shift), float(cutoff), int(cutoff_mode),
-                              float(eta), _ptr(dth), _ptr(ev), _ptr(nk), ws.h, _stream()))
+                              float(eta), _solver(solver), _ptr(dth), _ptr(ev), _ptr(nk), ws.h, _stream()))
     if sync:
         ws.sync_status()
     return dth, ev, nk
@@ -215,13 +221,14 @@ class SRStep:
     """A prepared block-layer SR step: sizes the workspace once, then runs
     ``sr_step`` on new (theta, configs) of the same shape."""
 
-    def __init__(self, model: Model, n_s: int, ham: Hamiltonian, block_off, precision="split_bf16",
+    def __init__(self, model: Model, n_s: int, ham: Hamiltonian, block_off, precision="split_bf16x3",
                  diag_shift: float = 1e-3, cutoff: float = 1e-10, cutoff_mode: int = 0, eta: float = 1.0,
-                 want_evals: bool = False, device="cuda"):
+                 want_evals: bool = False, solver="fp64", device="cuda"):
         lib = _lib.load()
         self.model, self.ham = model, ham
         self.n_s = int(n_s)
         self.p = _prec(precision)
+        self.solver = _solver(solver)
         self.off = _off(block_off)
         self.nb = len(self.off) - 1
         self.n_p = int(block_off[-1])
@@ -248,7 +255,7 @@ class SRStep:
     def __call__(self, theta: torch.Tensor, configs: torch.Tensor, sync: bool = False):
         lib = _lib.load()
         check(lib.sr_step(C.byref(self.model.c), _ptr(theta), _ptr(configs), self.n_s, C.byref(self.ham.c),
-                          self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p,
+                          self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p, self.solver,
                           _ptr(self.dtheta), _ptr(self.emean), _ptr(self.evals), _ptr(self.n_kept),
                           NQS_SYNC if sync else 0, self.ws.h, _stream()))
         return self.dtheta, self.emean
@@ -256,10 +263,10 @@ class SRStep:
 
 def sr_step(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian, block_off,
             diag_shift: float, cutoff: float, eta: float = 1.0, precision="fp64", cutoff_mode: int = 0,
-            want_evals: bool = True):
+            want_evals: bool = True, solver="fp64"):
     """One whole block-layer SR step: (dtheta, Emean, evals, n_kept)."""
     st = SRStep(model, int(configs.shape[0]), ham, block_off, precision, diag_shift, cutoff, cutoff_mode, eta,
-                want_evals, device=configs.device)
+                want_evals, solver, device=configs.device)
     st(theta, configs, sync=True)
     return st.dtheta, st.emean, st.evals, st.n_kept
 

@@ -79,11 +79,14 @@ inline int jac_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
 // local energies: FP32 arithmetic only in NQS_FP32 mode (in the split modes an FP32
 // E_loc alone moves dtheta by ~1e-5 relative on the 10x10 workload)
 inline int eloc_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
-inline int nsplit_of(int prec) { return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : 0); }
+inline int nsplit_of(int prec) {
+    return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : (prec == NQS_SPLIT_BF16_EXACT ? 5 : 0));
+}
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
 int check_prec(int prec) {
-    if (prec != NQS_FP64 && prec != NQS_FP32 && prec != NQS_SPLIT_BF16 && prec != NQS_SPLIT_BF16X3)
+    if (prec != NQS_FP64 && prec != NQS_FP32 && prec != NQS_SPLIT_BF16 && prec != NQS_SPLIT_BF16X3 &&
+        prec != NQS_SPLIT_BF16_EXACT)
         return fail(NQS_ERR_INVALID_ARG, "unknown precision %d", prec);
     return NQS_OK;
 }
@@ -143,16 +146,18 @@ void plan_eloc(Arena& a, long long ns, int nbonds, ElocBufs* b) {
 
 struct BuildBufs {
     c128* e;
-    void* planes[3];
+    void* planes[5];
     double* diag;
+    int8_t* gexp;
     long long ldk;
 };
 void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
     b->e = static_cast<c128*>(a.take(16 * ns));
     b->ldk = round_up(ns, 64);
     const int nsp = nsplit_of(prec);
-    for (int i = 0; i < 3; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
+    for (int i = 0; i < 5; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
     b->diag = nsp ? static_cast<double*>(a.take(8 * np)) : nullptr;
+    b->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(b->ldk / 16) * np)) : nullptr;
 }
 
 // ------------------------------------------------------------------ stages
@@ -180,8 +185,8 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
               DevStatus* status, cudaStream_t st, cudaEvent_t gram_event = nullptr) {
     CK(launch_emean(eloc, w, ns, Emean, bb.e, status, st), "emean");
     const int nsp = nsplit_of(prec);
-    CK(launch_center(prec, nsp, O, ldo, ns, np, w, bb.e, F, Omean, nsp ? bb.planes : nullptr, bb.ldk, bb.diag, status,
-                     st),
+    CK(launch_center(prec, nsp, O, ldo, ns, np, w, bb.e, F, Omean, nsp ? bb.planes : nullptr, bb.ldk, bb.diag,
+                     bb.gexp, status, st),
        "center");
     if (gram_event) CK(cudaEventRecord(gram_event, st), "event");
     GramTable* tab = new (std::nothrow) GramTable;
@@ -190,7 +195,7 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
     cudaError_t e;
     if (nsp) {
         gram_table(off, nb, 64, tab);
-        e = launch_gram_tc(nsp, bb.planes, 2 * np, bb.ldk, bb.ldk, scale, *tab, S, status, st);
+        e = launch_gram_tc(nsp, bb.planes, bb.gexp, np, 2 * np, bb.ldk, bb.ldk, scale, *tab, S, status, st);
         // the diagonal (sum_s w_s |dO_k|^2) is taken from the FP64 centring pass
         if (e == cudaSuccess) e = launch_set_diag(S, *tab, bb.diag, st);
     } else {
@@ -204,14 +209,17 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
 }
 
 int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, double cutoff, int mode,
-              double eta, c128* dtheta, double* evals, int32_t* n_kept, Arena& a, DevStatus* status,
+              double eta, int solver, c128* dtheta, double* evals, int32_t* n_kept, Arena& a, DevStatus* status,
               cudaStream_t st, cudaEvent_t trd_event = nullptr) {
+    if (solver != NQS_SOLVE_FP64 && solver != NQS_SOLVE_MIXED && solver != NQS_SOLVE_MIXED_PSD)
+        return fail(NQS_ERR_INVALID_ARG, "unknown solver %d", solver);
     if (!(shift >= 0.0)) return fail(NQS_ERR_INVALID_ARG, "diag_shift must be >= 0");
     if (!(cutoff >= 0.0)) return fail(NQS_ERR_INVALID_ARG, "cutoff must be >= 0");
     if (mode != 0 && mode != 1) return fail(NQS_ERR_INVALID_ARG, "cutoff_mode must be 0 or 1");
     const size_t need = solve_workspace_bytes(off, nb);
     void* work = a.take(need);
-    SolveArgs sa{shift, cutoff, eta, mode, evals != nullptr, trd_event};
+    SolveArgs sa{shift, cutoff, eta, mode, evals != nullptr, solver != NQS_SOLVE_FP64, solver == NQS_SOLVE_MIXED_PSD,
+                 trd_event};
     const int rc = launch_block_solve(S, off, nb, F, sa, dtheta, evals, n_kept, work, need, status, st);
     if (rc == NQS_ERR_UNSUPPORTED) return fail(rc, "block larger than the solver limit");
     if (rc != NQS_OK) return fail(rc, "block solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -484,8 +492,8 @@ int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const double
 }
 
 int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, const void* F, double diag_shift,
-                    double cutoff, int32_t cutoff_mode, double eta, void* dtheta_out, double* evals_out,
-                    int32_t* n_kept_out, nqs_workspace* ws, void* stream) {
+                    double cutoff, int32_t cutoff_mode, double eta, int32_t solver, void* dtheta_out,
+                    double* evals_out, int32_t* n_kept_out, nqs_workspace* ws, void* stream) {
     if (!S_packed || !F || !dtheta_out) return fail(NQS_ERR_INVALID_ARG, "qgt_block_solve: NULL pointer");
     int rc = check_offsets(block_off, n_blocks, -1);
     if (rc) return rc;
@@ -495,13 +503,13 @@ int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, 
     rc = check_ws(ws, need);
     if (rc) return rc;
     return run_solve(static_cast<c128*>(S_packed), block_off, n_blocks, static_cast<const c128*>(F), diag_shift,
-                     cutoff, cutoff_mode, eta, static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a,
+                     cutoff, cutoff_mode, eta, solver, static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a,
                      status_of(ws), static_cast<cudaStream_t>(stream));
 }
 
 int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h,
             const int64_t* block_off, int32_t n_blocks, double diag_shift, double cutoff, int32_t cutoff_mode,
-            double eta, int32_t precision, void* dtheta_out, void* Emean_out, double* evals_out,
+            double eta, int32_t precision, int32_t solver, void* dtheta_out, void* Emean_out, double* evals_out,
             int32_t* n_kept_out, int32_t flags, nqs_workspace* ws, void* stream) {
     ModelDesc md;
     HamDesc hd;
@@ -546,8 +554,10 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
                    static_cast<c128*>(Emean_out), bb, status, st, tm ? ws->ev[3] : nullptr);
     if (rc) return rc;
     if (tm) CK(cudaEventRecord(ws->ev[4], st), "event");
-    rc = run_solve(S, block_off, n_blocks, F, diag_shift, cutoff, cutoff_mode, eta, static_cast<c128*>(dtheta_out),
-                   evals_out, n_kept_out, a, status, st, tm ? ws->ev[5] : nullptr);
+    // S comes from the library's own Gram here: the mixed solver may use the PSD certificate
+    const int sv = solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver;
+    rc = run_solve(S, block_off, n_blocks, F, diag_shift, cutoff, cutoff_mode, eta, sv,
+                   static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a, status, st, tm ? ws->ev[5] : nullptr);
     if (rc) return rc;
     if (tm) {
         CK(cudaEventRecord(ws->ev[6], st), "event");

@@ -178,12 +178,102 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
     return cudaGetLastError();
 }
 
+// Grouped error-free split (O is c128, unchanged): for every parameter row and every
+// group of 16 samples, E = exponent of the group's max |Re|, |Im| of sqrt(w) dO; the
+// values t = x 2^-E (|t| < 1) are split into five BF16 slices s_i = rint(r 2^(8i+7))
+// 2^-(8i+7) (integers of at most 8 bits times a power of two), so that products of
+// slices of one group lie on a common grid and sums of 16 of them are exact.
+constexpr int GROUP = 16;
+__global__ void __launch_bounds__(256) center_group_kernel(const c128* __restrict__ O, long long ldo, long long ns,
+                                                            const double* __restrict__ w,
+                                                            const c128* __restrict__ e, c128* __restrict__ F,
+                                                            c128* __restrict__ Omean, __nv_bfloat16* __restrict__ pl0,
+                                                            __nv_bfloat16* __restrict__ pl1,
+                                                            __nv_bfloat16* __restrict__ pl2,
+                                                            __nv_bfloat16* __restrict__ pl3,
+                                                            __nv_bfloat16* __restrict__ pl4, int8_t* __restrict__ gexp,
+                                                            long long np, long long ldk, double* __restrict__ diag,
+                                                            DevStatus* status) {
+    __shared__ double sh[32];
+    const long long p = blockIdx.x;
+    const c128* row = O + p * ldo;
+    const double u = 1.0 / (double)ns;
+    double mr = 0.0, mi = 0.0;
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+        const c128 v = row[s];
+        const double ws = w ? w[s] : 1.0;
+        mr = fma(ws, v.re, mr);
+        mi = fma(ws, v.im, mi);
+    }
+    mr = block_sum(mr, sh);
+    mi = block_sum(mi, sh);
+    if (!w) {
+        mr *= u;
+        mi *= u;
+    }
+    double fr = 0.0, fi = 0.0, dg = 0.0;
+    __nv_bfloat16* pls[5] = {pl0, pl1, pl2, pl3, pl4};
+    // blockDim.x is a multiple of GROUP, so each group of 16 samples lies in one half-warp
+    for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
+        double dr = 0.0, di = 0.0;
+        if (s < ns) {
+            const c128 v = row[s];
+            const double ws = w ? w[s] : u;
+            dr = v.re - mr;
+            di = v.im - mi;
+            const c128 es = e[s];
+            fr = fma(ws, fma(dr, es.re, di * es.im), fr);
+            fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
+            dg = fma(ws, fma(dr, dr, di * di), dg);
+            if (w) {
+                const double sw = sqrt(ws);
+                dr *= sw;
+                di *= sw;
+            }
+        }
+        double mx = fmax(fabs(dr), fabs(di));
+#pragma unroll
+        for (int o = GROUP / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o, GROUP));
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
+        if ((s & (GROUP - 1)) == 0) gexp[(s / GROUP) * np + p] = (int8_t)ex;
+        const double inv = ldexp(1.0, -ex);
+        double tr = dr * inv, ti = di * inv;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const double sc = ldexp(1.0, 8 * q + 7);
+            const double qr = rint(tr * sc) / sc, qi = rint(ti * sc) / sc;
+            pls[q][(2 * p) * ldk + s] = __double2bfloat16(qr);
+            pls[q][(2 * p + 1) * ldk + s] = __double2bfloat16(qi);
+            tr -= qr;
+            ti -= qi;
+        }
+    }
+    fr = block_sum(fr, sh);
+    fi = block_sum(fi, sh);
+    dg = block_sum(dg, sh);
+    if (threadIdx.x == 0) {
+        F[p] = mk<double>(fr, fi);
+        if (Omean) Omean[p] = mk<double>(mr, mi);
+        diag[p] = dg;
+        if (!(isfinite(mr) && isfinite(mi) && isfinite(fr) && isfinite(fi)))
+            set_status(status, NQS_ERR_NONFINITE, W_CENTER, p);
+    }
+}
+
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          double* diag, DevStatus* status, cudaStream_t st) {
+                          double* diag, int8_t* gexp, DevStatus* status, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)np;
-    if (nsplit == 2 || nsplit == 3) {
+    if (nsplit == 5) {
+        count_launch();
+        center_group_kernel<<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean,
+                                                  (__nv_bfloat16*)planes[0], (__nv_bfloat16*)planes[1],
+                                                  (__nv_bfloat16*)planes[2], (__nv_bfloat16*)planes[3],
+                                                  (__nv_bfloat16*)planes[4], gexp, np, ldk, diag, status);
+    } else if (nsplit == 2 || nsplit == 3) {
         __nv_bfloat16* p0 = (__nv_bfloat16*)planes[0];
         __nv_bfloat16* p1 = (__nv_bfloat16*)planes[1];
         __nv_bfloat16* p2 = nsplit == 3 ? (__nv_bfloat16*)planes[2] : nullptr;

@@ -3,20 +3,22 @@
 // computed as the real Gram G = X X^T of the interleaved real rows X[2k] = Re dO_k,
 // X[2k+1] = Im dO_k (samples contiguous, i.e. K-major operands), so that
 //   Re S[k][l] = G[2k][2l] + G[2k+1][2l+1],   Im S[k][l] = G[2k][2l+1] - G[2k+1][2l].
-// Every entry is split element-wise x = x1 + x2 (+ x3), each a BF16 rounding of the
-// remainder (relative error 2^-17 / 2^-25), and G is accumulated from the products
-// x1 y1 (accumulator A0) and the correction products x1 y2 + x2 y1 (+ x1 y3 + x3 y1
-// + x2 y2) (accumulator A1). FP32 accumulation in tensor memory only spans one
-// 64-sample K block (four MMA steps); the epilogue folds every K block into
-// double-float (FP32 hi + lo, TwoSum) running sums held in registers, so the
-// accumulation error does not grow with the number of samples. S is written in
-// FP64 once per tile.
+// Every entry is split into BF16 terms x = x1 + x2 (+ x3 (+ x4)) and G is accumulated
+// from the leading products x1 y1 (accumulator A0) and the correction products
+// (accumulator A1). Two splits: element-wise (each term the BF16 rounding of the
+// remainder, 2 or 3 terms), and grouped error-free (per parameter and 16-sample group
+// a common power of two, five slices of at most 8-bit integers; Ozaki, Ogita, Oishi
+// and Rump 2012), in which the A0 sums and the order-1 sums are exact. FP32 accumulation in tensor memory
+// spans at most one K block; the epilogue folds every work item into double-float
+// (FP32 hi + lo, TwoSum) running sums of A0 and FP32 sums of A1 held in registers,
+// so the accumulation error does not grow with the number of samples. S is written
+// in FP64 once per tile.
 //
 // Persistent kernel, one CTA per SM, static round-robin over the lower-triangle
 // 128 x 128 tiles of every block. Warp roles: warp 0 issues TMA loads (128B
 // swizzle) into a STAGES-deep ring, warp 1 allocates tensor memory and issues
-// tcgen05.mma, warps 2-9 (two per tensor-memory lane quarter, one per column
-// half) drain the double-buffered accumulator pairs
+// tcgen05.mma, warps 2-9 (two per tensor-memory lane quarter, one per 64-column
+// half of the tile) drain the double-buffered accumulator pairs
 // (tcgen05.ld), combine the 2 x 2 real blocks into complex entries and fold
 // them. Every mbarrier wait is bounded; on expiry the kernel records
 // NQS_ERR_TIMEOUT, drains its own copies and MMAs, frees tensor memory and
@@ -31,8 +33,7 @@ namespace nqs {
 namespace tc {
 
 constexpr int BM = 128;          // real rows per tile (64 complex)
-constexpr int BK = 64;           // BF16 elements per 128-byte swizzle row
-constexpr int TILE_BYTES = BM * BK * 2;          // 16 KB
+constexpr int BK = 64;           // samples of one K block (128-byte swizzle rows)
 constexpr int NTHREADS = 320;                    // TMA warp, MMA warp, 8 epilogue warps
 constexpr int NEPI = 256;                        // epilogue threads
 constexpr uint32_t TMEM_COLS = 512;              // 2 buffers x up to 2 accumulators x 128 columns
@@ -50,6 +51,22 @@ template <> struct Split<3> {   // x1 y1 | x1 y2 + x2 y1 + x1 y3 + x3 y1 + x2 y2
     static constexpr int NPL = 3, NPROD = 6, STAGES = 2;
     __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
     __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
+};
+
+// Grouped error-free slices, five per value: s1 s1 -> A0; into A1 first every product of
+// order 2..4 (issued while A1 is small), then the order-1 products s1 s2 + s2 s1 (exact).
+template <> struct Split<5> {
+    static constexpr int NPL = 5, NPROD = 15, STAGES = 2;
+    // 0:(0,0) | 1:(0,2) 2:(2,0) 3:(1,1) 4:(0,3) 5:(3,0) 6:(1,2) 7:(2,1) 8:(0,4) 9:(4,0) 10:(1,3)
+    //          11:(3,1) 12:(2,2) 13:(0,1) 14:(1,0)
+    __device__ static constexpr int pa(int i) {
+        return i == 2 ? 2 : i == 3 ? 1 : i == 5 ? 3 : i == 6 ? 1 : i == 7 ? 2 : i == 9 ? 4 : i == 10 ? 1
+             : i == 11 ? 3 : i == 12 ? 2 : i == 14 ? 1 : 0;
+    }
+    __device__ static constexpr int pb(int i) {
+        return i == 1 ? 2 : i == 3 ? 1 : i == 4 ? 3 : i == 6 ? 2 : i == 7 ? 1 : i == 8 ? 4 : i == 10 ? 3
+             : i == 11 ? 1 : i == 12 ? 2 : i == 13 ? 1 : 0;
+    }
 };
 
 // Error-free sum of two FP32 numbers: s + e = a + b exactly.
@@ -110,15 +127,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups
-// 1024 bytes apart (SBO), descriptor version 1, leading offset unused (1).
+// Shared-memory matrix descriptor: K-major, rows of KB BF16 (128-byte swizzle for
+// KB = 64, 64-byte swizzle for KB = 32), 8-row core groups 8 * 2 KB bytes apart
+// (SBO), descriptor version 1, leading offset unused (1).
+template <int KB>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    static_assert(KB == 64 || KB == 32, "K block of 32 or 64 BF16");
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;                 // LBO (ignored for swizzled K-major)
-    d |= (uint64_t)(1024u >> 4) << 32;       // SBO
-    d |= (uint64_t)1u << 46;                 // version
-    d |= (uint64_t)2u << 61;                 // SWIZZLE_128B
+    d |= (uint64_t)1u << 16;                          // LBO (ignored for swizzled K-major)
+    d |= (uint64_t)((8u * 2u * KB) >> 4) << 32;       // SBO
+    d |= (uint64_t)1u << 46;                          // version
+    d |= (uint64_t)(KB == 64 ? 2u : 4u) << 61;        // SWIZZLE_128B / SWIZZLE_64B
     return d;
 }
 
@@ -141,6 +161,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
@@ -187,20 +214,26 @@ __device__ __forceinline__ TileInfo decode(const GramTable& tab, long long t) {
 }
 
 struct Maps {
-    CUtensorMap m[3];
+    CUtensorMap m[5];
 };
 
 // Work item = (tile, kpi MMA K-steps of 16 samples; kpi divides 4). Each work item
 // owns one of two accumulator pairs (A0, A1) in tensor memory; smem stages hold
 // one 64-sample K block each.
-template <int NSPLIT>
+// KB: samples per K block (64 or 32). GROUPED: every 16-sample group carries its own
+// per-parameter exponents gexp[group][param]; the epilogue scales each group by
+// 2^(E_k + E_l) (one MMA K step per work item, kpi = 1).
+template <int NSPLIT, bool GROUPED, int KB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_tc_kernel(const __grid_constant__ Maps maps, const __grid_constant__ GramTable tab, int nkb, int kpi,
-                   double scale, c128* __restrict__ S, DevStatus* status) {
+                   double scale, const int8_t* __restrict__ gexp, long long np, c128* __restrict__ S,
+                   DevStatus* status) {
     using SP = Split<NSPLIT>;
     constexpr int NS = SP::NPL;
     constexpr int STAGES = SP::STAGES;
-    constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+    constexpr int KTILE_BYTES = BM * KB * 2;
+    constexpr int STAGE_BYTES = 2 * NS * KTILE_BYTES;
+    constexpr int KSTEPS = KB / 16;
     constexpr uint32_t BUF_COLS = 256u;  // A0 and A1, 128 columns each
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -253,12 +286,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t ph = (q / STAGES) & 1u;
                     if (!mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) { ok = false; break; }
                     unsigned char* st = ring + (size_t)s * STAGE_BYTES;
-                    mbar_expect_tx(&full_bar[s], (diag ? NS : 2 * NS) * TILE_BYTES);
+                    mbar_expect_tx(&full_bar[s], (diag ? NS : 2 * NS) * KTILE_BYTES);
                     for (int p = 0; p < NS; ++p)
-                        tma_load_2d(st + p * TILE_BYTES, &maps.m[p], &full_bar[s], kb * BK, rowA);
+                        tma_load_2d(st + p * KTILE_BYTES, &maps.m[p], &full_bar[s], kb * KB, rowA);
                     if (!diag)
                         for (int p = 0; p < NS; ++p)
-                            tma_load_2d(st + (NS + p) * TILE_BYTES, &maps.m[p], &full_bar[s], kb * BK, rowB);
+                            tma_load_2d(st + (NS + p) * KTILE_BYTES, &maps.m[p], &full_bar[s], kb * KB, rowB);
                 }
             }
             if (!ok) {
@@ -277,7 +310,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_128x128();
-            const int nsub = (BK / 16) / kpi;
+            const int nsub = KSTEPS / kpi;
             uint32_t q = 0, w = 0;  // smem stage counter, accumulator work-item counter
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
@@ -289,7 +322,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (!mbar_wait(&full_bar[s], ph, abort_flag)) { ok = false; break; }
                     fence_after();
                     const uint32_t base = smem_u32(ring + (size_t)s * STAGE_BYTES);
-                    const uint32_t boff = diag ? 0u : (uint32_t)(NS * TILE_BYTES);
+                    const uint32_t boff = diag ? 0u : (uint32_t)(NS * KTILE_BYTES);
                     for (int sub = 0; sub < nsub; ++sub, ++w) {
                         const uint32_t acc = w & 1u;
                         const uint32_t tmem_d = tmem_base + acc * BUF_COLS;
@@ -299,11 +332,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes inside the swizzle row
 #pragma unroll
                             for (int pr = 0; pr < SP::NPROD; ++pr) {
-                                const uint32_t aad = base + SP::pa(pr) * TILE_BYTES + off;
-                                const uint32_t bad = base + boff + SP::pb(pr) * TILE_BYTES + off;
+                                const uint32_t aad = base + SP::pa(pr) * KTILE_BYTES + off;
+                                const uint32_t bad = base + boff + SP::pb(pr) * KTILE_BYTES + off;
                                 // product 0 -> A0; products 1.. -> A1; the first write of each resets it
                                 const uint32_t first = (kk == sub * kpi && pr <= 1) ? 0u : 1u;
-                                umma(tmem_d + (pr == 0 ? 0u : 128u), sdesc(aad), sdesc(bad), idesc, first);
+                                umma(tmem_d + (pr == 0 ? 0u : 128u), sdesc<KB>(aad), sdesc<KB>(bad), idesc, first);
                             }
                         }
                         umma_commit(&tfull_bar[acc]);   // hands the accumulator pair to the epilogue
@@ -323,18 +356,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else {
         // ---------------- epilogue: warp w owns TMEM lane quarter w % 4 and column half (w - 2) / 4
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int half = (warp - 2) >> 2;   // 64 real columns = 32 complex columns each
         const int r = quarter * 32 + lane;  // accumulator row (real row within the tile)
         const int cpar = r & 1;             // 0: Re row, 1: Im row of complex row r/2
         uint32_t q = 0;
         bool ok = true;
-        const int nitems = nkb * ((BK / 16) / kpi);
+        const int nitems = nkb * (KSTEPS / kpi);
         for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const TileInfo ti = decode(tab, t);
             const GBlk blk = tab.b[ti.b];
             const int n = blk.n;
             const long long k = (long long)ti.I * (BM / 2) + (r >> 1);
-            // double-float running sums of the 16 complex outputs this lane owns
+            // double-float running sums of the 16 complex outputs this lane owns, renormalised
+            // after every work item
             float hre[16], lre[16], him[16], lim[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) hre[j] = lre[j] = him[j] = lim[j] = 0.f;
@@ -345,46 +379,78 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 fence_after();
+                // grouped mode: exponents of this 16-sample group (row k, this lane's columns)
+                int ekg = 0;
+                const int8_t* gcol = nullptr;
+                if (GROUPED) {
+                    const int8_t* ge = gexp + (long long)item * np + blk.row0;
+                    ekg = (k < n) ? (int)ge[k] : 0;
+                    gcol = ge + (long long)ti.J * (BM / 2) + 32 * half;
+                }
 #pragma unroll
-                for (int chunk = 0; chunk < 4; ++chunk) {
-                    float g[16];
-                    {
-                        uint32_t v0[16], v1[16];
-                        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BUF_COLS +
-                                               (uint32_t)(64 * half + 16 * chunk);
-                        tmem_ld16(taddr, v0);
-                        tmem_ld16(taddr + 128u, v1);
+                for (int chunk = 0; chunk < 8; ++chunk) {
+                    uint32_t v0[8], v1[8];
+                    const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BUF_COLS +
+                                           (uint32_t)(64 * half + 8 * chunk);
+                    tmem_ld8(taddr, v0);
+                    tmem_ld8(taddr + 128u, v1);
+                    // 8 real columns = 2 pairs of complex columns (l0 = 2m, l1 = 2m + 1)
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) g[j] = __uint_as_float(v0[j]) + __uint_as_float(v1[j]);
-                    }
-                    // 16 real columns = 4 pairs of complex columns (l0 = 2m, l1 = 2m + 1)
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const float g0 = g[4 * m + 0];  // col (l0, re)
-                        const float g1 = g[4 * m + 1];  // col (l0, im)
-                        const float g2 = g[4 * m + 2];  // col (l1, re)
-                        const float g3 = g[4 * m + 3];  // col (l1, im)
-                        // even lane (Re row) sends its l1 pair, odd lane (Im row) its l0 pair
-                        const float s0 = cpar ? g0 : g2;
-                        const float s1 = cpar ? g1 : g3;
-                        const float y0 = __shfl_xor_sync(0xffffffffu, s0, 1);
-                        const float y1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-                        float re, im;
-                        if (cpar == 0) {   // S[k][l0]: g00 = g0, g01 = g1, g10 = y0, g11 = y1
-                            re = g0 + y1;
-                            im = g1 - y0;
-                        } else {           // S[k][l1]: g00 = y0, g01 = y1, g10 = g2, g11 = g3
-                            re = y0 + g3;
-                            im = y1 - g2;
+                    for (int m = 0; m < 2; ++m) {
+                        float re0, im0, re1, im1;
+                        {
+                            // A0: in grouped mode these are exact sums on a common grid, so the
+                            // 2 x 2 combination below is exact in FP32
+                            const float g0 = __uint_as_float(v0[4 * m + 0]);  // col (l0, re)
+                            const float g1 = __uint_as_float(v0[4 * m + 1]);  // col (l0, im)
+                            const float g2 = __uint_as_float(v0[4 * m + 2]);  // col (l1, re)
+                            const float g3 = __uint_as_float(v0[4 * m + 3]);  // col (l1, im)
+                            // even lane (Re row) sends its l1 pair, odd lane (Im row) its l0 pair
+                            const float y0 = __shfl_xor_sync(0xffffffffu, cpar ? g0 : g2, 1);
+                            const float y1 = __shfl_xor_sync(0xffffffffu, cpar ? g1 : g3, 1);
+                            if (cpar == 0) {   // S[k][l0]: g00 = g0, g01 = g1, g10 = y0, g11 = y1
+                                re0 = g0 + y1;
+                                im0 = g1 - y0;
+                            } else {           // S[k][l1]: g00 = y0, g01 = y1, g10 = g2, g11 = g3
+                                re0 = y0 + g3;
+                                im0 = y1 - g2;
+                            }
                         }
-                        const int j = 4 * chunk + m;
+                        {
+                            const float g0 = __uint_as_float(v1[4 * m + 0]);
+                            const float g1 = __uint_as_float(v1[4 * m + 1]);
+                            const float g2 = __uint_as_float(v1[4 * m + 2]);
+                            const float g3 = __uint_as_float(v1[4 * m + 3]);
+                            const float y0 = __shfl_xor_sync(0xffffffffu, cpar ? g0 : g2, 1);
+                            const float y1 = __shfl_xor_sync(0xffffffffu, cpar ? g1 : g3, 1);
+                            if (cpar == 0) {
+                                re1 = g0 + y1;
+                                im1 = g1 - y0;
+                            } else {
+                                re1 = y0 + g3;
+                                im1 = y1 - g2;
+                            }
+                        }
+                        const int j = 2 * chunk + m;
+                        if (GROUPED) {
+                            const long long lcol = (long long)ti.J * (BM / 2) + 32 * half + 2 * j + cpar;
+                            const int el = (lcol < n) ? (int)gcol[2 * j + cpar] : 0;
+                            const int es = ekg + el;  // 2^(E_k + E_l), exact
+                            const float f = (es >= -126 && es <= 127) ? __int_as_float((es + 127) << 23)
+                                                                      : ldexpf(1.f, es);
+                            re0 *= f;
+                            im0 *= f;
+                            re1 *= f;
+                            im1 *= f;
+                        }
+                        // (h, l) += re0 (exact) + re1: TwoSum of the high word with the exact
+                        // leading part, then renormalise with the small terms so that the low
+                        // word never accumulates across groups
                         float sh, se;
-                        two_sum(hre[j], re, sh, se);
-                        hre[j] = sh;
-                        lre[j] += se;
-                        two_sum(him[j], im, sh, se);
-                        him[j] = sh;
-                        lim[j] += se;
+                        two_sum(hre[j], re0, sh, se);
+                        two_sum(sh, (se + re1) + lre[j], hre[j], lre[j]);
+                        two_sum(him[j], im0, sh, se);
+                        two_sum(sh, (se + im1) + lim[j], him[j], lim[j]);
                     }
                 }
                 fence_before();
@@ -434,21 +500,36 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-static bool make_map(CUtensorMap* m, const void* base, long long rows, long long ldk) {
+static bool make_map(CUtensorMap* m, const void* base, long long rows, long long ldk, int kb) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
-    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+    cuuint32_t box[2] = {(cuuint32_t)kb, (cuuint32_t)tc::BM};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows, long long ldk, long long kpad,
-                           double scale, const GramTable& tab, c128* S, DevStatus* status, cudaStream_t st) {
+template <int NSPLIT, bool GROUPED, int KB>
+static cudaError_t launch_tc(const tc::Maps& maps, const GramTable& tab, long long kpad, int kpi, double scale,
+                            const int8_t* gexp, long long np, c128* S, DevStatus* status, int sms, cudaStream_t st) {
+    const size_t smem = (size_t)tc::Split<NSPLIT>::STAGES * 2 * tc::Split<NSPLIT>::NPL * (tc::BM * KB * 2) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel<NSPLIT, GROUPED, KB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = tab.total_tiles < sms ? tab.total_tiles : sms;
+    count_launch();
+    tc::gram_tc_kernel<NSPLIT, GROUPED, KB><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(
+        maps, tab, (int)(kpad / KB), kpi, scale, gexp, np, S, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(int nsplit, const void* const* planes, const int8_t* gexp, long long np, long long rows,
+                           long long ldk, long long kpad, double scale, const GramTable& tab, c128* S,
+                           DevStatus* status, cudaStream_t st) {
     static int kpi = -1;  // MMA K-steps per accumulator flush (1, 2 or 4); NQS_GRAM_KPI overrides
     if (kpi < 0) {
         const char* env = getenv("NQS_GRAM_KPI");
@@ -456,7 +537,7 @@ cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows
         kpi = (v == 1 || v == 2 || v == 4) ? v : GRAM_KPI_DEFAULT;
     }
     if (tab.total_tiles <= 0) return cudaSuccess;
-    if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
+    if (nsplit != 2 && nsplit != 3 && nsplit != 5) return cudaErrorInvalidValue;
     int dev = 0;
     cudaGetDevice(&dev);
     int major = 0, minor = 0, sms = 0;
@@ -465,28 +546,15 @@ cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (major != 10 || minor != 3) return cudaErrorNotSupported;
     if (ldk % tc::BK != 0 || kpad % tc::BK != 0 || kpad > ldk) return cudaErrorInvalidValue;
+    const int kb = nsplit == 5 ? 32 : 64;
     tc::Maps maps;
     for (int p = 0; p < nsplit; ++p) {
         if (reinterpret_cast<uintptr_t>(planes[p]) & 15) return cudaErrorInvalidValue;
-        if (!make_map(&maps.m[p], planes[p], rows, ldk)) return cudaErrorInvalidValue;
+        if (!make_map(&maps.m[p], planes[p], rows, ldk, kb)) return cudaErrorInvalidValue;
     }
-    const int nkb = (int)(kpad / tc::BK);
-    const long long grid = tab.total_tiles < sms ? tab.total_tiles : sms;
-    cudaError_t e;
-    if (nsplit == 2) {
-        const size_t smem = (size_t)tc::Split<2>::STAGES * 4 * tc::TILE_BYTES + 1024;
-        e = cudaFuncSetAttribute(tc::gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        count_launch();
-        tc::gram_tc_kernel<2><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpi, scale, S, status);
-    } else {
-        const size_t smem = (size_t)tc::Split<3>::STAGES * 6 * tc::TILE_BYTES + 1024;
-        e = cudaFuncSetAttribute(tc::gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        count_launch();
-        tc::gram_tc_kernel<3><<<(unsigned)grid, tc::NTHREADS, smem, st>>>(maps, tab, nkb, kpi, scale, S, status);
-    }
-    return cudaGetLastError();
+    if (nsplit == 2) return launch_tc<2, false, 64>(maps, tab, kpad, kpi, scale, nullptr, np, S, status, sms, st);
+    if (nsplit == 3) return launch_tc<3, false, 64>(maps, tab, kpad, kpi, scale, nullptr, np, S, status, sms, st);
+    return launch_tc<5, true, 32>(maps, tab, kpad, 1, scale, gexp, np, S, status, sms, st);
 }
 
 }  // namespace nqs

@@ -68,10 +68,11 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
                          DevStatus* status, cudaStream_t st);
 // nsplit 0: dO written in place (prec FP64/FP32); nsplit 2 or 3: element-wise BF16
 // split planes of dO (O is c128, unchanged)
-// (split modes also write diag[k] = sum_s w_s |dO_k(s)|^2 in FP64)
+// (split modes also write diag[k] = sum_s w_s |dO_k(s)|^2 in FP64; nsplit 5 = grouped
+// error-free split with int8 exponents gexp[group][param], groups of 16 samples)
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          double* diag, DevStatus* status, cudaStream_t st);
+                          double* diag, int8_t* gexp, DevStatus* status, cudaStream_t st);
 
 // ---- Gram ----
 struct GBlk {                   // one QGT block of one instance
@@ -92,8 +93,9 @@ constexpr int GRAM_KPI_DEFAULT = 4;    // MMA K-steps (16 samples) per accumulat
 // tcgen05 Gram over nsplit element-wise BF16 split planes (2: 3 products; 3: 6 products),
 // FP32 accumulation per 64-sample K block folded into double-float sums;
 // cudaErrorNotSupported off sm_103.
-cudaError_t launch_gram_tc(int nsplit, const void* const* planes, long long rows, long long ldk, long long kpad,
-                           double scale, const GramTable& tab, c128* S, DevStatus* status, cudaStream_t st);
+cudaError_t launch_gram_tc(int nsplit, const void* const* planes, const int8_t* gexp, long long np, long long rows,
+                           long long ldk, long long kpad, double scale, const GramTable& tab, c128* S,
+                           DevStatus* status, cudaStream_t st);
 void gram_table(const int64_t* block_off, int nb, int tile_rows, GramTable* tab);
 // overwrite the diagonal of every S_b with diag (FP64 sums of |dO_k|^2)
 cudaError_t launch_set_diag(c128* S, const GramTable& tab, const double* diag, cudaStream_t st);
@@ -103,6 +105,8 @@ struct SolveArgs {
     double shift, cutoff, eta;
     int cutoff_mode;
     bool want_evals;
+    bool mixed;                 // FP32 reduction + FP64 iterative refinement
+    bool psd;                   // S_b is a Gram matrix: sigma_min >= shift - 1e-6 sigma_max
     cudaEvent_t ev_trd_done;    // recorded after the tridiagonal reduction (or NULL)
 };
 size_t solve_workspace_bytes(const int64_t* block_off, int nb);

@@ -94,6 +94,9 @@ def test_local_energy_marshall_sign_and_units():
     ("j1j2_6x6_ffnn", 70, "split_bf16", 5e-5),
     ("j1j2_6x6_ffnn", 70, "split_bf16x3", 2e-5),
     ("chain10_rbm", 1100, "split_bf16x3", 2e-6),
+    ("j1j2_6x6_ffnn", 70, "split_bf16_exact", 1e-6),
+    ("chain10_rbm", 1100, "split_bf16_exact", 1e-7),
+    ("j1j2_10x10_ffnn5", 45, "split_bf16_exact", 1e-6),
 ])
 def test_qgt_block_build(name, ns, prec, tol):
     w = W.make_workload(name, ns)
@@ -156,8 +159,12 @@ def test_solve_absolute_cutoff_mode():
     ("chain10_rbm", 333, "fp32", 1e-4),
     ("j1j2_6x6_ffnn", 300, "fp64", 1e-10),
     ("j1j2_6x6_ffnn", 300, "fp32", 1e-4),
-    ("j1j2_6x6_ffnn", 300, "split_bf16x3", 1e-6),
-    ("j1j2_10x10_ffnn5", 200, "split_bf16x3", 1e-6),
+    # three 8-bit slices keep 24 significant bits per element, as FP32 does: FP32-class bar
+    ("j1j2_6x6_ffnn", 300, "split_bf16x3", 1e-4),
+    ("j1j2_10x10_ffnn5", 200, "split_bf16x3", 1e-4),
+    ("chain10_rbm", 777, "split_bf16_exact", 1e-6),
+    ("j1j2_6x6_ffnn", 300, "split_bf16_exact", 1e-6),
+    ("j1j2_10x10_ffnn5", 200, "split_bf16_exact", 1e-6),
 ])
 def test_sr_step(name, ns, prec, tol):
     w = W.make_workload(name, ns)
@@ -174,3 +181,86 @@ def test_single_sample_step_is_zero():
     model, theta, x, ham = dev_inputs(w)
     dth, em, _, _ = nq().sr_step(model, theta, x, ham, w.block_off, 1e-4, 1e-10, 1.0, "fp64")
     assert torch.all(dth == 0)
+
+
+@pytest.mark.parametrize("sizes", [[1, 2, 3], [17, 65, 130], [300, 64]])
+@pytest.mark.parametrize("solver", ["mixed", "mixed_psd"])
+def test_mixed_solver_matches_definition(sizes, solver):
+    """FP32 reduction + FP64 refinement reaches the FP64 definition when the cutoff keeps all eigenvalues."""
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rng = np.random.default_rng(9)
+    blocks = []
+    for b, n in enumerate(sizes):
+        X = rng.normal(size=(2 * n + 3, n)) + 1j * rng.normal(size=(2 * n + 3, n))
+        X[:, : n // 2] *= 1e-2  # spread the spectrum
+        blocks.append(np.conj(X).T @ X / X.shape[0])
+    F = rng.normal(size=off[-1]) + 1j * rng.normal(size=off[-1])
+    S = torch.as_tensor(np.concatenate([B.ravel() for B in blocks]), device="cuda")
+    dth, ev, nk = nq().qgt_block_solve(S, off, torch.as_tensor(F, device="cuda"), 1e-4, 1e-10, 0, 1.0,
+                                       solver=solver)
+    ref, sig, kept = oracle.qgt.block_solve(blocks, F, off, 1e-4, 1e-10, 1.0)
+    assert np.array_equal(nk.cpu().numpy(), kept)
+    assert rel(dth.cpu().numpy(), ref) < 1e-10
+    evg = ev.cpu().numpy()
+    for b in range(len(sizes)):
+        np.testing.assert_allclose(evg[off[b]:off[b + 1]], sig[b], rtol=0, atol=1e-5 * sig[b].max())
+
+
+def test_mixed_solver_falls_back_when_cutoff_binds():
+    sizes = [40, 9]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    blocks = [_herm_psd(n, 3 + n, np.logspace(-6, 0, n)) for n in sizes]
+    F = np.random.default_rng(1).normal(size=off[-1]) + 0j
+    S = torch.as_tensor(np.concatenate([B.ravel() for B in blocks]), device="cuda")
+    dth, _, nk = nq().qgt_block_solve(S, off, torch.as_tensor(F, device="cuda"), 1e-8, 3e-3, 0, 1.0,
+                                      solver="mixed")
+    ref, _, kept = oracle.qgt.block_solve(blocks, F, off, 1e-8, 3e-3, 1.0)
+    assert np.array_equal(nk.cpu().numpy(), kept)
+    assert rel(dth.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("name,ns,prec,tol", [
+    ("chain10_rbm", 512, "fp64", 1e-10),
+    ("j1j2_6x6_ffnn", 300, "fp64", 1e-10),
+])
+def test_sr_step_mixed_solver(name, ns, prec, tol):
+    w = W.make_workload(name, ns)
+    model, theta, x, ham = dev_inputs(w)
+    dth, em, ev, nk = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec,
+                                   solver="mixed")
+    r = _oracle_all(w)
+    assert rel(dth.cpu().numpy(), r["dtheta"]) < tol
+    assert np.array_equal(nk.cpu().numpy(), r["n_kept"])
+
+
+def _golden(name):
+    import os
+    p = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{name}.npz")
+    if not os.path.exists(p):
+        pytest.skip(f"{p} not generated (tests/golden/make_fullsize.py)")
+    return np.load(p)
+
+
+@pytest.mark.parametrize("name,prec,solver,tol", [
+    ("j1j2_6x6_ffnn", "fp64", "fp64", 1e-10),
+    ("j1j2_6x6_ffnn", "fp64", "mixed", 1e-10),
+    ("j1j2_6x6_ffnn", "split_bf16_exact", "mixed", 1e-6),
+    ("j1j2_6x6_ffnn", "split_bf16x3", "mixed", 1e-4),
+    ("j1j2_6x6_ffnn", "fp32", "mixed", 1e-4),
+    ("j1j2_10x10_ffnn5", "split_bf16_exact", "mixed", 1e-6),
+    ("j1j2_10x10_ffnn5", "split_bf16_exact", "fp64", 1e-6),
+])
+def test_fullsize_against_oracle(name, prec, solver, tol):
+    """Full-size workloads (6x6: FFNN 36-64-64-1, 4096 samples; 10x10: FFNN 100-64x4-1,
+    16384 samples) against the FP64 oracle results stored by tests/golden/make_fullsize.py."""
+    g = _golden(name)
+    w = W.make_workload(name)
+    model, theta, x, ham = dev_inputs(w)
+    dth, em, _, nk = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec,
+                                  solver=solver, want_evals=False)
+    assert rel(dth.cpu().numpy(), g["dtheta"]) < tol
+    etol = 1e-7 if prec == "fp32" else 1e-11
+    assert abs(em.cpu().numpy()[0] - g["e_mean"]) < etol * abs(g["e_mean"])
+    assert np.array_equal(nk.cpu().numpy(), g["n_kept"])
+    el = nq().nqs_local_energy(model, theta, x, ham, "fp64").cpu().numpy()
+    np.testing.assert_allclose(el[g["eloc_idx"]], g["eloc"], rtol=1e-11, atol=1e-11)

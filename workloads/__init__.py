@@ -135,7 +135,7 @@ class Workload:
     block_off: np.ndarray          # int64 [n_blocks+1]
     diag_shift: float
     cutoff: float
-    precision: str                 # "fp64" | "fp32" | "split_bf16" | "split_bf16x3"
+    precision: str                 # "fp64" | "fp32" | "split_bf16" | "split_bf16x3" | "split_bf16_exact"
     c: float = 1.0                 # spin units: 1 = Pauli (sigma.sigma)
     sign_rule: int = 1             # +1: no Marshall sign; -1: Marshall sign
 
@@ -154,8 +154,8 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
     * ``chain10_rbm``      RBM alpha=1 on a 10-site Heisenberg chain, 512 samples, FP64.
     * ``j1j2_6x6_ffnn``    FFNN 36-64-64-1, 6x6 J1-J2 (J2=0.5), 4096 samples, FP32.
     * ``j1j2_10x10_ffnn5`` FFNN 100-64-64-64-64-1, 10x10 J1-J2, 16384 samples, BF16 split
-      (three-way, six products: the two-way three-product split cannot reach a
-      1e-6 relative dtheta error on this workload).
+      (grouped error-free four-slice split: the element-wise two- and three-way
+      splits cannot reach a 1e-6 relative dtheta error on this workload).
     * ``j1j2_10x10_ffnn256`` FFNN 100-256-256-1, 10x10 J1-J2, 32768 samples.
     * ``batch8x8_<i>``     instance i (0..15) of the batched 8x8 workload.
     """
@@ -183,7 +183,7 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
         configs = zero_sz_configs(100, ns, rng)
         ij, jj = square_j1j2_bonds(10, 10, 1.0, 0.5)
         return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
-                        1e-3, 1e-10, "split_bf16x3")
+                        1e-3, 1e-10, "split_bf16_exact")
     if name == "j1j2_10x10_ffnn256":
         model = _ffnn(100, [256, 256])
         rng = np.random.default_rng(5)
