@@ -186,6 +186,33 @@ NQS_API int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, cons
                     int32_t precision, void* S_packed, void* F_out, void* Omean_out,
                     void* Emean_out, nqs_workspace* ws, void* stream);
 
+/* qgt_block_build_static -- qgt_block_build without a workspace. The paper has no
+ * counterpart: this is an interface variant, not a step of the method.
+ * It is meant for callers that have no device memory to lend to the library, e.g. a
+ * plug-in interface that hands over only its input and output buffers, or a process
+ * whose device memory is entirely held by another allocator. The call allocates
+ * nothing: its only scratch, the centred local energies e_s (16 bytes per sample),
+ * lives in a fixed array in the library's own static device memory.
+ *   Arguments, layouts and results are those of qgt_block_build, with two limits:
+ *   precision  : NQS_FP64 or NQS_FP32 only (the split modes need n_p-sized planes);
+ *                any other value returns NQS_ERR_INVALID_ARG.
+ *   n_s        : at most NQS_STATIC_MAX_SAMPLES; larger n_s returns
+ *                NQS_ERR_INVALID_ARG before anything is launched.
+ * Set-up: the first call on each device (with that device current) looks up the
+ * device address of the static array once and caches it; make that first call
+ * outside any stream capture.
+ * Nothing in the static array has to start at zero: every element is written by the
+ * call before it is read.
+ * There is no device-side status: a non-finite O or E_loc shows as NaN/Inf in the
+ * outputs instead of in nqs_sync_status.
+ * Overlapping calls on one device (concurrent streams or host threads) share the one
+ * array and race: order them, e.g. on a single stream. */
+#define NQS_STATIC_MAX_SAMPLES 65536
+NQS_API int qgt_block_build_static(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const double* w,
+                           const int64_t* block_off, int32_t n_blocks, const void* eloc,
+                           int32_t precision, void* S_packed, void* F_out, void* Omean_out,
+                           void* Emean_out, void* stream);
+
 /* ---- per-block solver ----
  * NQS_SOLVE_FP64 : the Householder reduction, eigenvalues and solve all in FP64.
  * NQS_SOLVE_MIXED: the O(n^3) reduction runs in FP32 on a copy of S_b (FP64 units run

@@ -23,6 +23,7 @@ NQS_FP64, NQS_FP32, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SPLIT_BF16_EXACT = 0, 
 NQS_RBM, NQS_FFNN = 0, 1
 NQS_SYNC = 1
 NQS_SOLVE_FP64, NQS_SOLVE_MIXED, NQS_SOLVE_MIXED_PSD = 0, 1, 2
+NQS_STATIC_MAX_SAMPLES = 65536
 
 
 class nqs_model(C.Structure):
@@ -60,6 +61,7 @@ SIGNATURES = {
     "nqs_local_energy": (C.c_int, [MP, P, P, I64, HP, I32, P, P, P]),
     "nqs_connections": (C.c_int, [P, I64, HP, P, P, P, I64, C.POINTER(C.c_int64), P, P]),
     "qgt_block_build": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P, P]),
+    "qgt_block_build_static": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P]),
     "qgt_block_solve": (C.c_int, [P, OFF, I32, P, D, D, I32, D, I32, P, P, P, P, P]),
     "sr_step": (C.c_int, [MP, P, P, I64, HP, OFF, I32, D, D, I32, D, I32, I32, P, P, P, P, I32, P, P]),
     "nqs_stage_timing": (C.c_int, [P, I32]),

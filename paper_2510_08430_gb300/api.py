@@ -196,6 +196,25 @@ def qgt_block_build(O: torch.Tensor, n_s: int, block_off, eloc: torch.Tensor, pr
     return S, F, Om, Em
 
 
+def qgt_block_build_static(O: torch.Tensor, n_s: int, block_off, eloc: torch.Tensor, precision="fp64",
+                           w: Optional[torch.Tensor] = None):
+    """qgt_block_build without a workspace (fp64/fp32, n_s <= NQS_STATIC_MAX_SAMPLES);
+    same results. The outputs are allocated here by torch; the library call allocates nothing."""
+    lib = _lib.load()
+    p = _prec(precision)
+    off = _off(block_off)
+    nb = len(off) - 1
+    n_p = int(block_off[-1])
+    dev = O.device
+    S = torch.zeros(int(lib.qgt_packed_size(off, nb)), dtype=torch.complex128, device=dev)
+    F = torch.empty(n_p, dtype=torch.complex128, device=dev)
+    Om = torch.empty(n_p, dtype=torch.complex128, device=dev)
+    Em = torch.empty(1, dtype=torch.complex128, device=dev)
+    check(lib.qgt_block_build_static(_ptr(O), int(O.shape[1]), n_s, n_p, _ptr(w), off, nb, _ptr(eloc), p, _ptr(S),
+                                     _ptr(F), _ptr(Om), _ptr(Em), _stream()))
+    return S, F, Om, Em
+
+
 def qgt_block_solve(S: torch.Tensor, block_off, F: torch.Tensor, diag_shift: float, cutoff: float,
                     cutoff_mode: int = 0, eta: float = 1.0, want_evals: bool = True, solver="fp64",
                     ws: Optional[Workspace] = None, sync: bool = True):

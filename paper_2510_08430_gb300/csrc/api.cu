@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <new>
+#include <atomic>
 #include "internal.cuh"
 
 using namespace nqs;
@@ -568,3 +569,63 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- build without a workspace
+// qgt_block_build_static serves callers that cannot lend the library device memory (a
+// plug-in interface that passes only its input and output buffers, or a process whose
+// device memory another allocator holds in full). Its one scratch buffer, the centred
+// local energies, is this fixed array; nothing is allocated per call.
+static __device__ __align__(256) c128 g_static_e[NQS_STATIC_MAX_SAMPLES];
+
+namespace {
+
+constexpr int STATIC_MAX_DEVICES = 64;
+std::atomic<c128*> g_static_e_addr[STATIC_MAX_DEVICES];  // device address of g_static_e, per device
+
+// Set-up, once per device with that device current: look up where g_static_e lives.
+int static_scratch(c128** out) {
+    int dev = -1;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES)
+        return fail(NQS_ERR_UNSUPPORTED, "device ordinal %d beyond %d", dev, STATIC_MAX_DEVICES);
+    c128* p = g_static_e_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* q = nullptr;
+        CK(cudaGetSymbolAddress(&q, g_static_e), "cudaGetSymbolAddress");
+        p = static_cast<c128*>(q);
+        g_static_e_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return NQS_OK;
+}
+
+}  // namespace
+
+extern "C" int qgt_block_build_static(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const double* w,
+                                      const int64_t* block_off, int32_t n_blocks, const void* eloc,
+                                      int32_t precision, void* S_packed, void* F_out, void* Omean_out,
+                                      void* Emean_out, void* stream) {
+    if (precision != NQS_FP64 && precision != NQS_FP32)
+        return fail(NQS_ERR_INVALID_ARG, "qgt_block_build_static: precision %d (NQS_FP64 or NQS_FP32 only)",
+                    precision);
+    if (!O || !eloc || !S_packed || !F_out || n_s < 1 || n_p < 1 || ldo < n_s)
+        return fail(NQS_ERR_INVALID_ARG, "qgt_block_build_static: bad arguments");
+    if (n_s > NQS_STATIC_MAX_SAMPLES)
+        return fail(NQS_ERR_INVALID_ARG, "qgt_block_build_static: n_s = %lld exceeds the static scratch of %d samples",
+                    (long long)n_s, NQS_STATIC_MAX_SAMPLES);
+    int rc = check_offsets(block_off, n_blocks, n_p);
+    if (rc) return rc;
+    c128* e = nullptr;
+    rc = static_scratch(&e);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(launch_emean(static_cast<const c128*>(eloc), w, n_s, static_cast<c128*>(Emean_out), e, nullptr, st), "emean");
+    CK(launch_center(precision, 0, O, ldo, n_s, n_p, w, e, static_cast<c128*>(F_out), static_cast<c128*>(Omean_out),
+                     nullptr, 0, nullptr, nullptr, nullptr, st),
+       "center");
+    GramTable tab;  // host stack
+    gram_table(block_off, n_blocks, 64, &tab);
+    CK(launch_gram_simt(precision, O, ldo, n_s, w, w ? 1.0 : 1.0 / (double)n_s, tab, static_cast<c128*>(S_packed), st),
+       "gram");
+    return NQS_OK;
+}
