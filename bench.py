@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "block-SR steps/sec and Gram TFLOP/s (% of peak) at δθ rel err ≤1e-6 vs FP64"
 WORKLOAD = "j1j2_10x10_ffnn5"
+W_DEFAULT_NS = {"j1j2_6x6_ffnn": 4096, "j1j2_10x10_ffnn5": 16384}
 
 
 def parse():
@@ -42,16 +43,23 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--samples", type=int, default=None, help="override N_s (profiling of small cases)")
+    ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def workload_desc(w) -> dict:
+SOLVER_DESC = {"fp64": "FP64 Householder eigensolver",
+               "mixed": "FP32 Householder reduction + FP64-residual refinement (PSD certificate, FP64 fallback)"}
+
+
+def workload_desc(w, solver="mixed") -> dict:
     import numpy as np
     return {
         "workload": f"{w.name}: widths {list(w.model.widths)}, {w.bond_ij.shape[0]} bonds, "
-                    f"N_s={w.n_samples}, blocks {list(np.diff(w.block_off))}, {w.precision} Gram, FP64 solve",
+                    f"N_s={w.n_samples}, blocks {list(np.diff(w.block_off))}, {w.precision} Gram, "
+                    f"{SOLVER_DESC[solver]}",
+        "solver": solver,
         "n_s": int(w.n_samples),
         "n_p": int(w.model.n_params),
         "blocks": [int(v) for v in np.diff(w.block_off)],
@@ -64,7 +72,9 @@ def workload_desc(w) -> dict:
 
 def dtype_of(prec: str) -> str:
     return {"fp64": "f64", "fp32": "f32+f64", "split_bf16": "bf16 hi+lo (3 products, f32 acc)+f32+f64",
-            "split_bf16x3": "bf16 hi+mid+lo (6 products, f32 acc)+f32+f64"}[prec]
+            "split_bf16x3": "bf16 hi+mid+lo (6 products, f32 acc)+f32+f64",
+            "split_bf16_exact": "bf16 x5 grouped error-free split (15 products, f32 TMEM acc, double-float sums)"
+                                "+f32+f64"}[prec]
 
 
 # ------------------------------------------------------------------ counts
@@ -76,7 +86,7 @@ def gram_flops(w) -> tuple:
     full = float(np.sum(8.0 * nb * nb * ns))
     tiles = np.ceil(2 * nb / 128.0)
     kpad = np.ceil(ns / 64.0) * 64.0
-    nprod = {"split_bf16": 3, "split_bf16x3": 6}.get(w.precision, 1)
+    nprod = {"split_bf16": 3, "split_bf16x3": 6, "split_bf16_exact": 15}.get(w.precision, 1)
     issued = float(np.sum(tiles * (tiles + 1) / 2 * nprod * 2 * 128 * 128 * kpad))
     return alg, full, issued
 
@@ -199,6 +209,48 @@ def fp64_peak_tflops(torch) -> float:
     return 2.0 * n ** 3 / best / 1e12
 
 
+# ------------------------------------------------------------------ same-GPU comparisons
+def _timed_step(torch, step, theta, x):
+    step(theta, x)  # warm
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    d, _ = step(theta, x)
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e) / 1e3, d.cpu().numpy()
+
+
+def compare_steps(nq, torch, np, w, model, ham, theta, x, dth, solver) -> dict:
+    """The plain FP64 and FP32 GPU steps and the cheaper split variants on the same GPU and
+    inputs, each with its dtheta error against the FP64 GPU step and against the stored FP64
+    oracle result of this workload (tests/golden, written from the oracle alone)."""
+    out = {}
+    gold = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.npz")
+    ref = np.load(gold)["dtheta"] if os.path.exists(gold) and w.n_samples == W_DEFAULT_NS.get(w.name) else None
+
+    def err(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    st = nq.SRStep(model, w.n_samples, ham, w.block_off, "fp64", w.diag_shift, w.cutoff, solver="fp64")
+    t64, d64 = _timed_step(torch, st, theta, x)
+    del st
+    out["fp64_fp64solve"] = {"seconds": t64, "dtheta_rel_err_vs_oracle": err(d64, ref) if ref is not None else None}
+    out[f"{w.precision}_{solver}solve (timed line)"] = {
+        "dtheta_rel_err_vs_fp64_gpu": err(dth, d64),
+        "dtheta_rel_err_vs_oracle": err(dth, ref) if ref is not None else None}
+    for prec in ("fp32", "split_bf16", "split_bf16x3"):
+        if prec == w.precision:
+            continue
+        st = nq.SRStep(model, w.n_samples, ham, w.block_off, prec, w.diag_shift, w.cutoff, solver=solver)
+        t, d = _timed_step(torch, st, theta, x)
+        del st
+        out[f"{prec}_{solver}solve"] = {"seconds": t, "dtheta_rel_err_vs_fp64_gpu": err(d, d64),
+                                         "dtheta_rel_err_vs_oracle": err(d, ref) if ref is not None else None}
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank: int, world: int) -> None:
     import workloads as W
@@ -218,7 +270,7 @@ def run_reference(args, rank: int, world: int) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_desc(w),
+        "config": workload_desc(w, "fp64"),
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": info["cores"], "kind": "oracle",
                          "sample": info["sample"]},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -243,7 +295,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     theta = torch.as_tensor(w.theta, device="cuda")
     x = torch.as_tensor(w.configs, device="cuda")
     ham = nq.Hamiltonian(w.model.n_sites, w.bond_ij, w.bond_j, w.c, w.sign_rule)
-    step = nq.SRStep(model, w.n_samples, ham, w.block_off, w.precision, w.diag_shift, w.cutoff)
+    step = nq.SRStep(model, w.n_samples, ham, w.block_off, w.precision, w.diag_shift, w.cutoff, solver=args.solver)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -326,7 +378,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
-        "config": dict(workload_desc(w), parallelism=("replicas" if world > 1 else "single")),
+        "config": dict(workload_desc(w, args.solver), parallelism=("replicas" if world > 1 else "single")),
         "stage_ms": st_mean,
         "roofline": {"kernel": "tridiagonal_reduction (trd_* kernel sequence, FP64)", "bound": "alu",
                      "achieved": trd_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": trd_tf / fp64_peak,
@@ -343,33 +395,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
     }
-    if world == 1 and not args.no_fp64_compare and w.precision != "fp64":
-        st64 = nq.SRStep(model, w.n_samples, ham, w.block_off, "fp64", w.diag_shift, w.cutoff)
-        torch.cuda.synchronize()
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record()
-        d64, _ = st64(theta, x)
-        e.record()
-        e.synchronize()
-        d64 = d64.cpu().numpy()
-        line["fp64_gpu_step"] = {"seconds": s.elapsed_time(e) / 1e3,
-                                 "dtheta_rel_err_vs_fp64_gpu": float(np.linalg.norm(dth_split - d64) /
-                                                                     np.linalg.norm(d64))}
-        del st64
-        # the two-way (three-product) split on the same inputs, for the record
-        if w.precision == "split_bf16x3":
-            st2 = nq.SRStep(model, w.n_samples, ham, w.block_off, "split_bf16", w.diag_shift, w.cutoff)
-            st2(theta, x)
-            s.record()
-            d2, _ = st2(theta, x)
-            e.record()
-            e.synchronize()
-            d2 = d2.cpu().numpy()
-            line["split_bf16_3prod"] = {"seconds": s.elapsed_time(e) / 1e3,
-                                        "dtheta_rel_err_vs_fp64_gpu": float(np.linalg.norm(d2 - d64) /
-                                                                            np.linalg.norm(d64))}
-            del st2
+    if world == 1 and not args.no_fp64_compare:
+        line["comparisons"] = compare_steps(nq, torch, np, w, model, ham, theta, x, dth_split, args.solver)
     if world == 1 and not args.no_cpu_baseline:
         info = oracle_sample(w)
         line["cpu_baseline"] = {"value": 1.0 / info["seconds_per_step"], "unit": "steps/s", "cores": info["cores"],

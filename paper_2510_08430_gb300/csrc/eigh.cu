@@ -17,38 +17,10 @@
 //     Otherwise the eigenvectors Z of T come from implicit QL iterations with
 //     Wilkinson shifts and z = Z diag(keep/sigma) Z^T Q^H F_b.
 //  4. dtheta_b = -eta Q z by applying the reflectors in reverse order.
-#include "internal.cuh"
+#include "eigh.cuh"
 
 namespace nqs {
 
-constexpr int TB = 64;       // tile of the fused update + matvec
-constexpr int CH = 256;      // rows per CTA in the vector kernels
-constexpr int MAXCH = 512;   // max row chunks per block (n <= 131072)
-constexpr int QL_MAXN = 12000;
-
-struct EBlk {
-    long long off;    // offset of the block in length-n_p arrays
-    long long soff;   // offset of S_b in the packed matrix array
-    long long yoff;   // offset of the block's matvec partials
-    int n;
-    int T;            // ceil(n / TB)
-    int orig;         // index of the block in the caller's order
-    int pad;
-};
-struct EBTab {
-    int nb;
-    EBlk b[MAXB];
-};
-struct HouseP {       // per-block scalars of the current reflector
-    c128 scale;       // 1 / (alpha - beta)
-    c128 tau;
-};
-struct BlkInfo {
-    double sigma_max;
-    double thr;
-    int n_dropped;
-    int n_kept;
-};
 
 struct SolveLayout {
     size_t tab, d, e, e2, tau, f, v0, v1, w, x, z, ev, hp, info, pnorm, pvf, pxv, ypart, zmat, total;
@@ -84,7 +56,7 @@ static SolveLayout solve_layout(const int64_t* off, int nb) {
     L.info = take(sizeof(BlkInfo) * nb);
     L.pnorm = take(8ull * nb * MAXCH);
     L.pvf = take(16ull * nb * MAXCH);
-    L.pxv = take(16ull * nb * MAXCH);
+    L.pxv = take(16ull * nb * MAXDCH);
     L.ypart = take(16ull * ytot);
     L.zmat = take(8ull * ztot);
     L.total = p;
@@ -92,29 +64,6 @@ static SolveLayout solve_layout(const int64_t* off, int nb) {
 }
 
 
-struct SolveBufs {
-    const EBlk* tab;
-    c128* S;
-    double *d, *e, *e2, *ev;
-    c128 *tau, *f, *v0, *v1, *w, *x, *z;
-    HouseP* hp;
-    BlkInfo* info;
-    double* pnorm;
-    c128 *pvf, *pxv, *ypart;
-    double* zmat;
-};
-
-// Views used by the Householder reduction in precision R (FP64 exact path,
-// FP32 preconditioner of the mixed path). f == nullptr skips the Q^H F update.
-template <typename R> struct TrdBufs {
-    const EBlk* tab;
-    cx<R>* A;
-    cx<R> *v0, *v1, *w, *x, *ypart;
-    c128* f;
-    double *d, *e, *e2, *pnorm;
-    c128 *tau, *pvf, *pxv;
-    HouseP* hp;
-};
 
 __global__ void upload_tab_kernel(const EBTab tab, EBlk* dst) {
     for (int i = threadIdx.x; i < tab.nb; i += blockDim.x) dst[i] = tab.b[i];
@@ -124,290 +73,6 @@ __global__ void upload_tab_kernel(const EBTab tab, EBlk* dst) {
 __global__ void init_f_kernel(const c128* __restrict__ F, long long np, c128* __restrict__ f) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
         f[p] = F[p];
-}
-
-// K1: bring column i up to date (rank-2 update of step i-1), partial norms of rows >= i+2.
-template <typename R>
-__global__ void __launch_bounds__(CH) trd_col_kernel(TrdBufs<R> B, int i, const cx<R>* __restrict__ vprev) {
-    __shared__ double sh[32];
-    const EBlk blk = B.tab[blockIdx.y];
-    const int n = blk.n;
-    if (i > n - 1) return;
-    const long long r = (long long)i + (long long)blockIdx.x * CH + threadIdx.x;
-    if ((long long)i + (long long)blockIdx.x * CH >= n) return;  // whole CTA past the end
-    cx<R>* A = B.A + blk.soff;
-    double nrm = 0.0;
-    if (r < n) {
-        cx<R> a = A[r * n + i];
-        if (i >= 1) {
-            const cx<R>* vp = vprev + blk.off;
-            const cx<R>* wp = B.w + blk.off;
-            const cx<R> vpi = vp[i], wpi = wp[i];
-            const cx<R> vr = vp[r], wr = wp[r];
-            a = a - vr * cconj(wpi) - wr * cconj(vpi);
-        }
-        if (r == i) a.im = R(0);
-        A[r * n + i] = a;
-        if (r >= i + 2) nrm = (double)cabs2(a);
-    }
-    nrm = block_sum(nrm, sh);
-    if (threadIdx.x == 0) B.pnorm[(long long)blockIdx.y * MAXCH + blockIdx.x] = nrm;
-}
-
-// K2: Householder reflector of column i (LAPACK-style: beta real, H^H [alpha; x] = [beta; 0]).
-template <typename R>
-__global__ void trd_house_kernel(TrdBufs<R> B, int i, DevStatus* status) {
-    const EBlk blk = B.tab[blockIdx.x];
-    const int n = blk.n;
-    if (i > n - 1) return;
-    const cx<R>* A = B.A + blk.soff;
-    const int lane = threadIdx.x;
-    const int my_nch = (n - i + CH - 1) / CH;  // chunks written by trd_col_kernel for this block
-    double xn = 0.0;
-    for (int c = lane; c < my_nch; c += 32) xn += B.pnorm[(long long)blockIdx.x * MAXCH + c];
-    xn = warp_sum(xn);
-    if (lane != 0) return;
-    B.d[blk.off + i] = (double)A[(long long)i * n + i].re;
-    if (i > n - 2) return;
-    const c128 alpha = ccast<double>(A[(long long)(i + 1) * n + i]);
-    HouseP h;
-    double beta;
-    if (xn == 0.0 && alpha.im == 0.0) {
-        beta = alpha.re;
-        h.tau = mk<double>(0.0, 0.0);
-        h.scale = mk<double>(0.0, 0.0);
-    } else {
-        const double nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn);
-        beta = (alpha.re >= 0.0) ? -nrm : nrm;
-        h.tau = mk<double>((beta - alpha.re) / beta, -alpha.im / beta);
-        const c128 dnm = mk<double>(alpha.re - beta, alpha.im);
-        const double q = cabs2(dnm);
-        h.scale = mk<double>(dnm.re / q, -dnm.im / q);
-    }
-    if (!isfinite(beta) || !finite_cx(h.tau) || !finite_cx(h.scale))
-        set_status(status, NQS_ERR_NONFINITE, W_TRD, (long long)blk.orig * 1000000 + i);
-    B.e[blk.off + i] = beta;
-    B.e2[blk.off + i] = beta * beta;
-    B.tau[blk.off + i] = h.tau;
-    B.hp[blockIdx.x] = h;
-}
-
-// K3: form v (v[i+1] = 1), store it in vcur and in row i's upper part; partial v^H f.
-template <typename R>
-__global__ void __launch_bounds__(CH) trd_v_kernel(TrdBufs<R> B, int i, cx<R>* __restrict__ vcur) {
-    __shared__ double sh[32];
-    const EBlk blk = B.tab[blockIdx.y];
-    const int n = blk.n;
-    if (i > n - 2) return;
-    const long long base = (long long)i + 1 + (long long)blockIdx.x * CH;
-    if (base >= n) return;
-    const long long r = base + threadIdx.x;
-    cx<R>* A = B.A + blk.soff;
-    const HouseP h = B.hp[blockIdx.y];
-    const cx<R> scale = ccast<R>(h.scale);
-    c128 vf = mk<double>(0.0, 0.0);
-    if (r < n) {
-        const cx<R> v = (r == i + 1) ? mk<R>(R(1), R(0)) : A[r * n + i] * scale;
-        vcur[blk.off + r] = v;
-        A[(long long)i * n + r] = v;
-        if (B.f) cmacc(vf, ccast<double>(v), B.f[blk.off + r]);
-    }
-    if (B.f) {
-        vf.re = block_sum(vf.re, sh);
-        vf.im = block_sum(vf.im, sh);
-        if (threadIdx.x == 0) B.pvf[(long long)blockIdx.y * MAXCH + blockIdx.x] = vf;
-    }
-}
-
-// K4: on the trailing region [i+1, n)^2 (lower triangle, absolute 64-tiles):
-//   A -= v_{i-1} w_{i-1}^H + w_{i-1} v_{i-1}^H      (pending update, if i >= 1)
-//   y  = A v_i                                        (Hermitian matvec partials)
-template <typename R>
-__global__ void __launch_bounds__(256) trd_fused_kernel(TrdBufs<R> B, int i, const cx<R>* __restrict__ vprev,
-                                                         const cx<R>* __restrict__ vcur) {
-    __shared__ cx<R> sv[2][TB], svp[2][TB], swp[2][TB];
-    __shared__ cx<R> p2buf[16][TB + 1];
-    __shared__ cx<R> p1s[TB];
-    const EBlk blk = B.tab[blockIdx.y];
-    const int n = blk.n;
-    if (i > n - 2) return;
-    const int R0 = i + 1;
-    const int T = blk.T;
-    const int J0 = R0 / TB;
-    const long long cnt = (long long)(T - J0) * (T - J0 + 1) / 2;
-    const long long t = blockIdx.x;
-    if (t >= cnt) return;
-    long long ii = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-    while (ii * (ii + 1) / 2 > t) --ii;
-    const int I = J0 + (int)ii;
-    const int J = J0 + (int)(t - ii * (ii + 1) / 2);
-    const bool pend = i >= 1;
-    const int tid = threadIdx.x;
-    const cx<R> zero = mk<R>(R(0), R(0));
-    if (tid < 2 * TB) {
-        const int which = tid / TB, q = tid % TB;
-        const int g = (which == 0 ? I : J) * TB + q;
-        cx<R> vv = zero, vp = zero, wp = zero;
-        if (g < n && g >= R0) {
-            vv = vcur[blk.off + g];
-            if (pend) {
-                vp = vprev[blk.off + g];
-                wp = B.w[blk.off + g];
-            }
-        }
-        sv[which][q] = vv;
-        svp[which][q] = vp;
-        swp[which][q] = wp;
-    }
-    __syncthreads();
-    cx<R>* A = B.A + blk.soff;
-    const int tx = tid & 15, ty = tid >> 4;
-    cx<R> p1[4], p2[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) p1[a] = p2[a] = zero;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int r = ty + 16 * a;
-        const int rg = I * TB + r;
-#pragma unroll
-        for (int bq = 0; bq < 4; ++bq) {
-            const int c = tx + 16 * bq;
-            const int cg = J * TB + c;
-            if (rg < n && cg < n && cg >= R0 && rg >= cg) {
-                const long long idx = (long long)rg * n + cg;
-                cx<R> x = A[idx];
-                if (pend) {
-                    x = x - svp[0][r] * cconj(swp[1][c]) - swp[0][r] * cconj(svp[1][c]);
-                    if (rg == cg) x.im = R(0);
-                    A[idx] = x;
-                }
-                cmac(p1[a], x, sv[1][c]);
-                if (rg > cg) cmacc(p2[bq], x, sv[0][r]);
-            }
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-            p1[a].re += __shfl_xor_sync(0xffffffffu, p1[a].re, o);
-            p1[a].im += __shfl_xor_sync(0xffffffffu, p1[a].im, o);
-        }
-        if (tx == 0) p1s[ty + 16 * a] = p1[a];
-    }
-#pragma unroll
-    for (int bq = 0; bq < 4; ++bq) p2buf[ty][tx + 16 * bq] = p2[bq];
-    __syncthreads();
-    cx<R>* Y = B.ypart + blk.yoff;
-    if (tid < TB) {
-        cx<R> s2 = zero;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) s2 = s2 + p2buf[k][tid];
-        if (I == J) {
-            Y[((long long)I * T + I) * TB + tid] = p1s[tid] + s2;
-        } else {
-            Y[((long long)I * T + J) * TB + tid] = p1s[tid];
-            Y[((long long)J * T + I) * TB + tid] = s2;
-        }
-    }
-}
-
-// K5: y = sum of matvec partials, x = tau y, partial x^H v.
-template <typename R>
-__global__ void __launch_bounds__(CH) trd_w1_kernel(TrdBufs<R> B, int i, const cx<R>* __restrict__ vcur) {
-    __shared__ double sh[32];
-    const EBlk blk = B.tab[blockIdx.y];
-    const int n = blk.n;
-    if (i > n - 2) return;
-    const long long base = (long long)i + 1 + (long long)blockIdx.x * CH;
-    if (base >= n) return;
-    const long long r = base + threadIdx.x;
-    const c128 tau = B.hp[blockIdx.y].tau;
-    c128 xv = mk<double>(0.0, 0.0);
-    if (r < n) {
-        const int T = blk.T, J0 = (i + 1) / TB;
-        const int I = (int)(r / TB), rr = (int)(r % TB);
-        const cx<R>* Y = B.ypart + blk.yoff + (long long)I * T * TB + rr;
-        c128 y = mk<double>(0.0, 0.0);
-        for (int s = J0; s < T; ++s) y = y + ccast<double>(Y[(long long)s * TB]);
-        const c128 x = tau * y;
-        B.x[blk.off + r] = ccast<R>(x);
-        cmacc(xv, x, ccast<double>(vcur[blk.off + r]));
-    }
-    xv.re = block_sum(xv.re, sh);
-    xv.im = block_sum(xv.im, sh);
-    if (threadIdx.x == 0) B.pxv[(long long)blockIdx.y * MAXCH + blockIdx.x] = xv;
-}
-
-// K6: w = x - 0.5 tau (x^H v) v; f <- H^H f = f - conj(tau) v (v^H f).
-template <typename R>
-__global__ void __launch_bounds__(CH) trd_w2_kernel(TrdBufs<R> B, int i, const cx<R>* __restrict__ vcur) {
-    __shared__ c128 red[2];
-    const EBlk blk = B.tab[blockIdx.y];
-    const int n = blk.n;
-    if (i > n - 2) return;
-    const long long base = (long long)i + 1 + (long long)blockIdx.x * CH;
-    if (base >= n) return;
-    if (threadIdx.x < 32) {
-        const int my_nch = (n - i - 1 + CH - 1) / CH;  // chunks of rows [i+1, n)
-        c128 a = mk<double>(0.0, 0.0), b = a;
-        for (int c = threadIdx.x; c < my_nch; c += 32) {
-            a = a + B.pxv[(long long)blockIdx.y * MAXCH + c];
-            if (B.f) b = b + B.pvf[(long long)blockIdx.y * MAXCH + c];
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (threadIdx.x == 0) {
-            red[0] = a;
-            red[1] = b;
-        }
-    }
-    __syncthreads();
-    const long long r = base + threadIdx.x;
-    if (r >= n) return;
-    const c128 tau = B.hp[blockIdx.y].tau;
-    const c128 alpha = (-0.5) * (tau * red[0]);
-    const c128 v = ccast<double>(vcur[blk.off + r]);
-    B.w[blk.off + r] = ccast<R>(ccast<double>(B.x[blk.off + r]) + alpha * v);
-    if (B.f) {
-        const c128 g = cconj(tau) * red[1];
-        B.f[blk.off + r] = B.f[blk.off + r] - g * v;
-    }
-}
-
-// Householder reduction of every block of the table (blocks sorted by size, descending).
-template <typename R>
-static int trd_reduce(const TrdBufs<R>& B, const EBTab& tab, cudaStream_t st, DevStatus* status) {
-    int nmax = 0;
-    for (int j = 0; j < tab.nb; ++j) nmax = tab.b[j].n > nmax ? tab.b[j].n : nmax;
-    for (int i = 0; i < nmax; ++i) {
-        int act1 = 0, act2 = 0;  // blocks with n-1 >= i, with n-2 >= i
-        while (act1 < tab.nb && tab.b[act1].n - 1 >= i) ++act1;
-        while (act2 < tab.nb && tab.b[act2].n - 2 >= i) ++act2;
-        cx<R>* vcur = (i & 1) ? B.v1 : B.v0;
-        cx<R>* vprev = (i & 1) ? B.v0 : B.v1;
-        const int nch1 = (nmax - i + CH - 1) / CH;
-        count_launch();
-        trd_col_kernel<R><<<dim3(nch1, act1), CH, 0, st>>>(B, i, vprev);
-        count_launch();
-        trd_house_kernel<R><<<act1, 32, 0, st>>>(B, i, status);
-        if (act2 > 0) {
-            const int nch2 = (nmax - i - 1 + CH - 1) / CH;
-            count_launch();
-            trd_v_kernel<R><<<dim3(nch2, act2), CH, 0, st>>>(B, i, vcur);
-            const int T0 = tab.b[0].T, J0 = (i + 1) / TB;
-            const long long cnt = (long long)(T0 - J0) * (T0 - J0 + 1) / 2;
-            count_launch();
-            trd_fused_kernel<R><<<dim3((unsigned)cnt, act2), 256, 0, st>>>(B, i, vprev, vcur);
-            count_launch();
-            trd_w1_kernel<R><<<dim3(nch2, act2), CH, 0, st>>>(B, i, vcur);
-            count_launch();
-            trd_w2_kernel<R><<<dim3(nch2, act2), CH, 0, st>>>(B, i, vcur);
-        }
-        if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
-    }
-    return NQS_OK;
 }
 
 // ------------------------------------------------------------------ eigenvalues
@@ -449,21 +114,106 @@ __device__ double bisect_k(const double* d, const double* e2, int n, double shif
     return 0.5 * (lo + hi);
 }
 
-// One thread per block: sigma_max, threshold, number dropped.
-__global__ void eig_bounds_kernel(SolveBufs B, int nb, SolveArgs a, DevStatus* status) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nb) return;
+// Gershgorin bounds of T + shift I and the largest e^2, reduced over the CTA.
+__device__ void gersh_cta(const double* d, const double* e, const double* e2, int n, double shift, double* lo,
+                          double* hi, double* emax) {
+    __shared__ double rl[32], rh[32], re[32];
+    double gl = 1e300, gu = -1e300, em = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k < n - 1 ? fabs(e[k]) : 0.0);
+        gl = fmin(gl, d[k] + shift - r);
+        gu = fmax(gu, d[k] + shift + r);
+        if (k + 1 < n) em = fmax(em, e2[k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+        gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+        em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        rl[w] = gl;
+        rh[w] = gu;
+        re[w] = em;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k) {
+            gl = fmin(gl, rl[k]);
+            gu = fmax(gu, rh[k]);
+            em = fmax(em, re[k]);
+        }
+        const double span = fmax(fabs(gl), fabs(gu));
+        rl[0] = gl - 4.0 * 2.22e-16 * span - 1e-300;
+        rh[0] = gu + 4.0 * 2.22e-16 * span + 1e-300;
+        re[0] = em;
+    }
+    __syncthreads();
+    *lo = rl[0];
+    *hi = rh[0];
+    *emax = re[0];
+    __syncthreads();
+}
+
+// Eigenvalues k0 (first half of the CTA) and k1 (second half) of T + shift I by
+// multisection: per round each thread of a half takes the Sturm count at one of its
+// interior points, and the bracket of the wanted eigenvalue shrinks (half + 1)-fold.
+// Stops when both brackets are narrower than tol (absolute) or after 12 rounds.
+__device__ void multisect2(const double* d, const double* e2, int n, double shift, int k0, int k1, double lo0,
+                           double hi0, double pivmin, double tol, double* out0, double* out1) {
+    __shared__ double blo[2], bhi[2];
+    __shared__ int cnt[1024];
+    const int half = blockDim.x / 2;
+    const int g = threadIdx.x / half, t = threadIdx.x % half;
+    const int k = g ? k1 : k0;
+    if (threadIdx.x == 0) {
+        blo[0] = blo[1] = lo0;
+        bhi[0] = bhi[1] = hi0;
+    }
+    __syncthreads();
+    for (int round = 0; round < 12; ++round) {
+        const bool open0 = !(bhi[0] - blo[0] <= tol), open1 = !(bhi[1] - blo[1] <= tol);
+        if (!open0 && !open1) break;
+        const double lo = blo[g], hi = bhi[g];
+        const double x = lo + (hi - lo) * (double)(t + 1) / (double)(half + 1);
+        cnt[threadIdx.x] = sturm_count(d, e2, n, shift, x, pivmin);
+        __syncthreads();
+        if (t == 0) {
+            double nlo = lo, nhi = hi;
+            for (int s2 = 0; s2 < half; ++s2) {
+                const double xs = lo + (hi - lo) * (double)(s2 + 1) / (double)(half + 1);
+                if (cnt[g * half + s2] <= k) {
+                    nlo = xs;
+                } else {
+                    nhi = xs;
+                    break;
+                }
+            }
+            blo[g] = nlo;
+            bhi[g] = nhi;
+        }
+        __syncthreads();
+    }
+    *out0 = 0.5 * (blo[0] + bhi[0]);
+    *out1 = 0.5 * (blo[1] + bhi[1]);
+    __syncthreads();
+}
+
+// One CTA per block: sigma_max (multisection to full precision), threshold, number dropped.
+__global__ void __launch_bounds__(256) eig_bounds_kernel(SolveBufs B, int nb, SolveArgs a, DevStatus* status) {
+    const int j = blockIdx.x;
     const EBlk blk = B.tab[j];
     const int n = blk.n;
     const double* d = B.d + blk.off;
     const double* e = B.e + blk.off;
     const double* e2 = B.e2 + blk.off;
-    double lo, hi;
-    gersh(d, e, n, a.shift, &lo, &hi);
-    double emax = 0.0;
-    for (int k = 0; k + 1 < n; ++k) emax = fmax(emax, e2[k]);
+    double lo, hi, emax;
+    gersh_cta(d, e, e2, n, a.shift, &lo, &hi, &emax);
     const double pivmin = 1e-290 * fmax(1.0, emax);
-    const double smax = bisect_k(d, e2, n, a.shift, n - 1, lo, hi, pivmin);
+    double smax, smax2;
+    multisect2(d, e2, n, a.shift, n - 1, n - 1, lo, hi, pivmin, 4.0 * 2.22e-16 * fmax(fabs(lo), fabs(hi)), &smax,
+               &smax2);
+    if (threadIdx.x != 0) return;
     const double thr = a.cutoff_mode == 0 ? a.cutoff * smax : a.cutoff;
     int drop = sturm_count(d, e2, n, a.shift, thr, pivmin);
     // eigenvalues within rounding of thr count as dropped when the Sturm count says <= thr
@@ -710,53 +460,28 @@ __global__ void __launch_bounds__(512) back_kernel(SolveBufs B, int nb, double e
 // residual r = F - (S + lambda I) x uses the FP64 S and the correction applies the
 // FP32 factorisation, x += Q (T + lambda I)^{-1} Q^H r. The iteration converges to
 // the FP64 solution when the FP32 factors approximate S to better than 1/kappa.
-constexpr int QNB = 32;      // reflectors per panel in the Q formation
-constexpr int QT = 64;       // tile of the Q formation kernels
-constexpr int REF_MAXIT = 30;
-constexpr double REF_TOL = 1e-14;
-
-struct MixBufs {
-    const EBlk* tab;
-    const c128* S;        // FP64 S (lower triangles), packed
-    c64* Sf;              // FP32 copy, reduced in place (reflectors in the upper rows)
-    c64* Q;               // explicit FP32 Q per block, packed like S
-    c64* Tf;              // T factors: per block ceil((n-1)/QNB) panels x QNB x QNB
-    long long* toff;      // per slot offset into Tf
-    c64* W;               // per block QNB x n scratch (T V^H Q' of the current panel)
-    double *d, *e;        // FP32-reduced tridiagonal (stored in FP64)
-    double *piv, *lmul;   // LDL^T of T + lambda I
-    c128 *x, *r;          // refinement iterate and residual (FP64)
-    c64 *r32, *y32, *w32; // FP32 work vectors
-    c64* ypart;           // Q^H r partial sums [chunk][np]
-    c128* hpart;          // FP64 Hermitian matvec partials (T^2 x 64 per block)
-    double* rn;           // per slot ||r||^2 partials [MAXCH]
-    double* fn;           // per slot ||F||^2
-    int* done;            // per slot converged flag
-    int* fallback;        // per slot: cutoff may drop an eigenvalue (needs the FP64 path)
-};
 
 __global__ void to_fp32_kernel(const c128* __restrict__ S, long long n, c64* __restrict__ Sf) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         Sf[i] = ccast<float>(S[i]);
 }
 
-// One thread per block: FP32-based bounds; a block needs the FP64 path when an
-// eigenvalue might fall on the dropped side of the cutoff within the FP32 error.
-__global__ void mix_cert_kernel(SolveBufs B, MixBufs M, int nb, SolveArgs a, DevStatus* status) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nb) return;
+// One CTA per block: FP32-based bounds; a block needs the FP64 path when an eigenvalue
+// might fall on the dropped side of the cutoff within the FP32 error. The bounds need
+// only ~1e-10 relative accuracy (the certificate allows 4e-5).
+__global__ void __launch_bounds__(256) mix_cert_kernel(SolveBufs B, MixBufs M, int nb, SolveArgs a, DevStatus* status) {
+    const int j = blockIdx.x;
     const EBlk blk = B.tab[j];
     const int n = blk.n;
     const double* d = M.d + blk.off;
     const double* e = M.e + blk.off;
     const double* e2 = B.e2 + blk.off;
-    double lo, hi;
-    gersh(d, e, n, a.shift, &lo, &hi);
-    double emax = 0.0;
-    for (int k = 0; k + 1 < n; ++k) emax = fmax(emax, e2[k]);
+    double lo, hi, emax;
+    gersh_cta(d, e, e2, n, a.shift, &lo, &hi, &emax);
     const double pivmin = 1e-290 * fmax(1.0, emax);
-    const double smax = bisect_k(d, e2, n, a.shift, n - 1, lo, hi, pivmin);
-    const double smin = bisect_k(d, e2, n, a.shift, 0, lo, hi, pivmin);
+    double smax, smin;
+    multisect2(d, e2, n, a.shift, n - 1, 0, lo, hi, pivmin, 1e-10 * fmax(fabs(lo), fabs(hi)), &smax, &smin);
+    if (threadIdx.x != 0) return;
     const double err = 4e-5 * fabs(smax);  // bound on the FP32 reduction's eigenvalue error
     const double thr_hi = a.cutoff_mode == 0 ? a.cutoff * (smax + err) : a.cutoff;
     // a Gram matrix plus shift has no eigenvalue below shift beyond its own rounding
@@ -826,312 +551,6 @@ __global__ void __launch_bounds__(256) qt_factor_kernel(SolveBufs B, MixBufs M) 
     }
 }
 
-__global__ void q_identity_kernel(SolveBufs B, MixBufs M) {
-    const EBlk blk = B.tab[blockIdx.y];
-    const long long nn = (long long)blk.n * blk.n;
-    c64* Q = M.Q + blk.soff;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
-        Q[i] = (i / blk.n == i % blk.n) ? mk<float>(1.f, 0.f) : mk<float>(0.f, 0.f);
-}
-
-// W[:, c-tile] = T (V^H Q'[:, c-tile]) for panel p; Q' = Q[i0+1:, i0+1:].
-__global__ void __launch_bounds__(256) q_w_kernel(SolveBufs B, MixBufs M, int p) {
-    __shared__ c64 Vs[32][QNB + 1];
-    __shared__ c64 Qs[32][QT + 1];
-    __shared__ c64 Ws[QNB][QT + 1];
-    const EBlk blk = B.tab[blockIdx.y];
-    const int n = blk.n;
-    const int i0 = p * QNB;
-    if (i0 >= n - 1) return;
-    const int nbp = (n - 1 - i0) < QNB ? (n - 1 - i0) : QNB;
-    const int m = n - i0 - 1;
-    const int c0 = blockIdx.x * QT;
-    if (c0 >= m) return;
-    const c64* A = M.Sf + blk.soff;
-    const c64* Q = M.Q + blk.soff;
-    const int tid = threadIdx.x;
-    // thread -> (j = tid / 8 in [0,32), columns cc = tid % 8 + 8 q, q = 0..7)
-    const int jj = tid >> 3, cl = tid & 7;
-    c64 acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = mk<float>(0.f, 0.f);
-    for (int r0 = 0; r0 < m; r0 += 32) {
-        for (int idx = tid; idx < 32 * QNB; idx += 256) {
-            const int rr = idx / QNB, j = idx % QNB;
-            const int r = r0 + rr;  // local row in [0, m): global row i0 + 1 + r
-            c64 v = mk<float>(0.f, 0.f);
-            if (r < m && j < nbp && r >= j) v = A[(long long)(i0 + j) * n + (i0 + 1 + r)];
-            Vs[rr][j] = v;
-        }
-        for (int idx = tid; idx < 32 * QT; idx += 256) {
-            const int rr = idx / QT, c = idx % QT;
-            const int r = r0 + rr;
-            c64 v = mk<float>(0.f, 0.f);
-            if (r < m && c0 + c < m) v = Q[(long long)(i0 + 1 + r) * n + (i0 + 1 + c0 + c)];
-            Qs[rr][c] = v;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-            const c64 v = Vs[rr][jj];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) cmacc(acc[q], v, Qs[rr][cl + 8 * q]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) Ws[jj][cl + 8 * q] = acc[q];
-    __syncthreads();
-    // W = T Ws (T upper triangular, QNB x QNB)
-    const c64* T = M.Tf + M.toff[blockIdx.y] + (long long)p * QNB * QNB;
-    c64* Wout = M.W + (long long)blk.off * QNB;  // [QNB][n] per block
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int c = cl + 8 * q;
-        c64 s = mk<float>(0.f, 0.f);
-        for (int b = jj; b < QNB; ++b) cmac(s, T[jj * QNB + b], Ws[b][c]);
-        if (c0 + c < m) Wout[(long long)jj * n + c0 + c] = s;
-    }
-}
-
-// Q'[r-tile, c-tile] -= V[r-tile, :] W[:, c-tile]
-__global__ void __launch_bounds__(256) q_update_kernel(SolveBufs B, MixBufs M, int p) {
-    __shared__ c64 Vs[QT][QNB + 1];
-    __shared__ c64 Ws[QNB][QT + 1];
-    const EBlk blk = B.tab[blockIdx.z];
-    const int n = blk.n;
-    const int i0 = p * QNB;
-    if (i0 >= n - 1) return;
-    const int nbp = (n - 1 - i0) < QNB ? (n - 1 - i0) : QNB;
-    const int m = n - i0 - 1;
-    const int r0 = blockIdx.y * QT, c0 = blockIdx.x * QT;
-    if (r0 >= m || c0 >= m) return;
-    const c64* A = M.Sf + blk.soff;
-    c64* Q = M.Q + blk.soff;
-    const c64* Win = M.W + (long long)blk.off * QNB;
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < QT * QNB; idx += 256) {
-        const int rr = idx / QNB, j = idx % QNB;
-        const int r = r0 + rr;
-        c64 v = mk<float>(0.f, 0.f);
-        if (r < m && j < nbp && r >= j) v = A[(long long)(i0 + j) * n + (i0 + 1 + r)];
-        Vs[rr][j] = v;
-    }
-    for (int idx = tid; idx < QNB * QT; idx += 256) {
-        const int j = idx / QT, c = idx % QT;
-        Ws[j][c] = (c0 + c < m && j < nbp) ? Win[(long long)j * n + c0 + c] : mk<float>(0.f, 0.f);
-    }
-    __syncthreads();
-    const int tx = tid & 15, ty = tid >> 4;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int rr = ty + 16 * a;
-        const int r = r0 + rr;
-        if (r >= m) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int cc = tx + 16 * b;
-            const int c = c0 + cc;
-            if (c >= m) continue;
-            c64 s = mk<float>(0.f, 0.f);
-#pragma unroll 8
-            for (int j = 0; j < QNB; ++j) cmac(s, Vs[rr][j], Ws[j][cc]);
-            const long long idx = (long long)(i0 + 1 + r) * n + (i0 + 1 + c);
-            Q[idx] = Q[idx] - s;
-        }
-    }
-}
-
-// Refinement init: x = 0, r = F, ||F||^2.
-__global__ void ref_init_kernel(SolveBufs B, MixBufs M, const c128* __restrict__ F) {
-    __shared__ double sh[32];
-    const EBlk blk = B.tab[blockIdx.x];
-    double s = 0.0;
-    for (int k = threadIdx.x; k < blk.n; k += blockDim.x) {
-        const c128 f = F[blk.off + k];
-        M.x[blk.off + k] = mk<double>(0.0, 0.0);
-        M.r[blk.off + k] = f;
-        M.r32[blk.off + k] = ccast<float>(f);
-        s += cabs2(f);
-    }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) {
-        M.fn[blockIdx.x] = s;
-        M.done[blockIdx.x] = (s == 0.0) ? 1 : 0;
-    }
-}
-
-// y partials over 256-row chunks: ypart[chunk][off + j] = sum_{i in chunk} conj(Q[i][j]) r32[i]
-__global__ void __launch_bounds__(256) ref_qh_kernel(SolveBufs B, MixBufs M, long long np) {
-    __shared__ c64 rs[256];
-    const EBlk blk = B.tab[blockIdx.z];
-    if (M.done[blockIdx.z] || M.fallback[blockIdx.z]) return;
-    const int n = blk.n;
-    const int i0 = blockIdx.y * 256;
-    if (i0 >= n || (int)(blockIdx.x * 256) >= n) return;
-    const int i1 = (i0 + 256) < n ? (i0 + 256) : n;
-    if (i0 + (int)threadIdx.x < n) rs[threadIdx.x] = M.r32[blk.off + i0 + threadIdx.x];
-    __syncthreads();
-    const int j = blockIdx.x * 256 + threadIdx.x;
-    if (j >= n) return;
-    const c64* Q = M.Q + blk.soff;
-    c64 acc = mk<float>(0.f, 0.f);
-    for (int i = i0; i < i1; ++i) cmacc(acc, Q[(long long)i * n + j], rs[i - i0]);
-    M.ypart[(long long)blockIdx.y * np + blk.off + j] = acc;
-}
-
-// w = (T + shift I)^{-1} (sum of the y partials), one thread per block (sequential LDL^T solve).
-__global__ void ref_tri_kernel(SolveBufs B, MixBufs M, int nb, long long np) {
-    const int jb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (jb >= nb) return;
-    if (M.done[jb] || M.fallback[jb]) return;
-    const EBlk blk = B.tab[jb];
-    const int n = blk.n;
-    const int nch = (n + 255) / 256;
-    const double* piv = M.piv + blk.off;
-    const double* l = M.lmul + blk.off;
-    c64* w = M.w32 + blk.off;
-    c128 u = mk<double>(0.0, 0.0);
-    for (int k = 0; k < n; ++k) {
-        c128 y = mk<double>(0.0, 0.0);
-        for (int c = 0; c < nch; ++c) y = y + ccast<double>(M.ypart[(long long)c * np + blk.off + k]);
-        u = (k == 0) ? y : y - l[k - 1] * u;
-        w[k] = ccast<float>(u);  // forward-eliminated values
-    }
-    c128 z = (1.0 / piv[n - 1]) * ccast<double>(w[n - 1]);
-    w[n - 1] = ccast<float>(z);
-    for (int k = n - 2; k >= 0; --k) {
-        z = (1.0 / piv[k]) * ccast<double>(w[k]) - l[k] * z;
-        w[k] = ccast<float>(z);
-    }
-}
-
-// x += Q w (warp per row), FP32 products accumulated then added to the FP64 iterate.
-__global__ void __launch_bounds__(256) ref_q_kernel(SolveBufs B, MixBufs M) {
-    const EBlk blk = B.tab[blockIdx.y];
-    if (M.done[blockIdx.y] || M.fallback[blockIdx.y]) return;
-    const int n = blk.n;
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (row >= n) return;
-    const c64* Q = M.Q + blk.soff + (long long)row * n;
-    const c64* w = M.w32 + blk.off;
-    c64 acc = mk<float>(0.f, 0.f);
-    for (int j = lane; j < n; j += 32) cmac(acc, Q[j], w[j]);
-    acc = warp_sum(acc);
-    if (lane == 0) M.x[blk.off + row] = M.x[blk.off + row] + ccast<double>(acc);
-}
-
-// Hermitian matvec partials of S x over absolute 64-tiles of the lower triangle (FP64).
-__global__ void __launch_bounds__(256) ref_hemv_kernel(SolveBufs B, MixBufs M) {
-    __shared__ c128 xs[2][TB];
-    __shared__ c128 p2buf[16][TB + 1];
-    __shared__ c128 p1s[TB];
-    const EBlk blk = B.tab[blockIdx.y];
-    if (M.done[blockIdx.y] || M.fallback[blockIdx.y]) return;
-    const int n = blk.n;
-    const int T = blk.T;
-    const long long t = blockIdx.x;
-    if (t >= (long long)T * (T + 1) / 2) return;
-    long long ii = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-    while (ii * (ii + 1) / 2 > t) --ii;
-    const int I = (int)ii, J = (int)(t - ii * (ii + 1) / 2);
-    const int tid = threadIdx.x;
-    if (tid < 2 * TB) {
-        const int which = tid / TB, q = tid % TB;
-        const int g = (which == 0 ? I : J) * TB + q;
-        xs[which][q] = g < n ? M.x[blk.off + g] : mk<double>(0.0, 0.0);
-    }
-    __syncthreads();
-    const c128* S = M.S + blk.soff;
-    const int tx = tid & 15, ty = tid >> 4;
-    c128 p1[4], p2[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) p1[a] = p2[a] = mk<double>(0.0, 0.0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int r = ty + 16 * a;
-        const int rg = I * TB + r;
-#pragma unroll
-        for (int bq = 0; bq < 4; ++bq) {
-            const int c = tx + 16 * bq;
-            const int cg = J * TB + c;
-            if (rg < n && cg < n && rg >= cg) {
-                c128 v = S[(long long)rg * n + cg];
-                if (rg == cg) v.im = 0.0;
-                cmac(p1[a], v, xs[1][c]);
-                if (rg > cg) cmacc(p2[bq], v, xs[0][r]);
-            }
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-            p1[a].re += __shfl_xor_sync(0xffffffffu, p1[a].re, o);
-            p1[a].im += __shfl_xor_sync(0xffffffffu, p1[a].im, o);
-        }
-        if (tx == 0) p1s[ty + 16 * a] = p1[a];
-    }
-#pragma unroll
-    for (int bq = 0; bq < 4; ++bq) p2buf[ty][tx + 16 * bq] = p2[bq];
-    __syncthreads();
-    c128* Y = M.hpart + blk.yoff;
-    if (tid < TB) {
-        c128 s2 = mk<double>(0.0, 0.0);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) s2 = s2 + p2buf[k][tid];
-        if (I == J) {
-            Y[((long long)I * T + I) * TB + tid] = p1s[tid] + s2;
-        } else {
-            Y[((long long)I * T + J) * TB + tid] = p1s[tid];
-            Y[((long long)J * T + I) * TB + tid] = s2;
-        }
-    }
-}
-
-// r = F - (S + shift I) x, FP32 copy of r, ||r||^2 partials.
-__global__ void __launch_bounds__(CH) ref_res_kernel(SolveBufs B, MixBufs M, const c128* __restrict__ F, double shift) {
-    __shared__ double sh[32];
-    const EBlk blk = B.tab[blockIdx.y];
-    if (M.done[blockIdx.y] || M.fallback[blockIdx.y]) return;
-    const int n = blk.n;
-    const int r0 = blockIdx.x * CH;
-    if (r0 >= n) return;
-    const int r = r0 + threadIdx.x;
-    double s = 0.0;
-    if (r < n) {
-        const int T = blk.T, I = r / TB, rr = r % TB;
-        const c128* Y = M.hpart + blk.yoff + (long long)I * T * TB + rr;
-        c128 y = mk<double>(0.0, 0.0);
-        for (int k = 0; k < T; ++k) y = y + Y[(long long)k * TB];
-        const c128 x = M.x[blk.off + r];
-        const c128 res = F[blk.off + r] - y - shift * x;
-        M.r[blk.off + r] = res;
-        M.r32[blk.off + r] = ccast<float>(res);
-        s = cabs2(res);
-    }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) M.rn[(long long)blockIdx.y * MAXCH + blockIdx.x] = s;
-}
-
-__global__ void ref_conv_kernel(SolveBufs B, MixBufs M, int nb, int last, DevStatus* status) {
-    const int jb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (jb >= nb) return;
-    if (M.done[jb] || M.fallback[jb]) return;
-    const EBlk blk = B.tab[jb];
-    const int nch = (blk.n + CH - 1) / CH;
-    double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += M.rn[(long long)jb * MAXCH + c];
-    if (!(s <= REF_TOL * REF_TOL * M.fn[jb])) {
-        if (!isfinite(s)) set_status(status, NQS_ERR_NONFINITE, W_SOLVE, blk.orig);
-        else if (last) set_status(status, NQS_ERR_NOT_CONVERGED, W_SOLVE, blk.orig);
-        return;
-    }
-    M.done[jb] = 1;
-}
-
 __global__ void ref_out_kernel(SolveBufs B, MixBufs M, double eta, c128* __restrict__ dtheta,
                                int32_t* __restrict__ n_kept) {
     const EBlk blk = B.tab[blockIdx.x];
@@ -1186,31 +605,29 @@ static void build_table(const int64_t* block_off, int nb, Built* bt) {
 
 struct SolveLayoutAll {
     SolveLayout L;
-    size_t sf, q, tf, toff, wq, piv, lmul, mx, mr, r32, y32, w32, ypq, hp, rn, fn, done, fb, total;
+    size_t sf, tf, toff, pdot, bar, piv, lmul, mx, mr, r32, y32, w32, hp, rn, fn, done, fb, total;
 };
 
 static SolveLayoutAll layout_all(const int64_t* off, int nb) {
     SolveLayoutAll A{};
     A.L = solve_layout(off, nb);
     const long long np = off[nb];
-    long long sq = 0, ytot = 0, tfe = 0;
-    int nmax = 0;
+    long long sq = 0, ytot = 0, tfe = 0, totch = 0;
     for (int b = 0; b < nb; ++b) {
         const long long n = off[b + 1] - off[b];
         sq += n * n;
         const long long T = (n + TB - 1) / TB;
         ytot += T * T * TB;
         tfe += ((n - 1 + QNB - 1) / QNB) * QNB * QNB;
-        nmax = n > nmax ? (int)n : nmax;
+        totch += (n + CH - 1) / CH;
     }
-    const int qch = (nmax + 255) / 256;
     size_t p = A.L.total;
     auto take = [&](size_t bytes) { size_t at = p; p += al(bytes); return at; };
     A.sf = take(8ull * sq);
-    A.q = take(8ull * sq);
     A.tf = take(8ull * (tfe > 0 ? tfe : 1));
     A.toff = take(8ull * nb);
-    A.wq = take(8ull * QNB * np);
+    A.pdot = take(8ull * 2 * totch * QNB);
+    A.bar = take(64);
     A.piv = take(8ull * np);
     A.lmul = take(8ull * np);
     A.mx = take(16ull * np);
@@ -1218,9 +635,8 @@ static SolveLayoutAll layout_all(const int64_t* off, int nb) {
     A.r32 = take(8ull * np);
     A.y32 = take(8ull * np);
     A.w32 = take(8ull * np);
-    A.ypq = take(8ull * qch * np);
     A.hp = take(16ull * ytot);
-    A.rn = take(8ull * nb * MAXCH);
+    A.rn = take(8ull * nb * MAXDCH);
     A.fn = take(8ull * nb);
     A.done = take(4ull * nb);
     A.fb = take(4ull * nb);
@@ -1263,11 +679,11 @@ static int solve_fp64(SolveBufs& B, const EBTab& tab, int nmax, const c128* F, c
     T.pvf = B.pvf;
     T.pxv = B.pxv;
     T.hp = B.hp;
-    int rc = trd_reduce<double>(T, tab, st, status);
+    int rc = launch_trd_persist<double>(T, tab, B.bar, status, st);
     if (rc) return rc;
     if (a.ev_trd_done) cudaEventRecord(a.ev_trd_done, st);
     count_launch();
-    eig_bounds_kernel<<<(nb + 63) / 64, 64, 0, st>>>(B, nb, a, status);
+    eig_bounds_kernel<<<nb, 256, 0, st>>>(B, nb, a, status);
     if (a.want_evals && evals) {
         count_launch();
         eig_all_kernel<<<dim3((nmax + 127) / 128, nb), 128, 0, st>>>(B, nb, a.shift, B.ev);
@@ -1324,6 +740,7 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     B.pxv = reinterpret_cast<c128*>(W + L.pxv);
     B.ypart = reinterpret_cast<c128*>(W + L.ypart);
     B.zmat = reinterpret_cast<double*>(W + L.zmat);
+    B.bar = reinterpret_cast<unsigned*>(W + LA.bar);
     const long long np = block_off[nb];
     count_launch();
     upload_tab_kernel<<<1, 256, 0, st>>>(tab, const_cast<EBlk*>(B.tab));
@@ -1335,10 +752,9 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     M.tab = B.tab;
     M.S = S;
     M.Sf = reinterpret_cast<c64*>(W + LA.sf);
-    M.Q = reinterpret_cast<c64*>(W + LA.q);
     M.Tf = reinterpret_cast<c64*>(W + LA.tf);
     M.toff = reinterpret_cast<long long*>(W + LA.toff);
-    M.W = reinterpret_cast<c64*>(W + LA.wq);
+    M.pdot = reinterpret_cast<c64*>(W + LA.pdot);
     M.d = B.d;
     M.e = B.e;
     M.piv = reinterpret_cast<double*>(W + LA.piv);
@@ -1348,7 +764,6 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     M.r32 = reinterpret_cast<c64*>(W + LA.r32);
     M.y32 = reinterpret_cast<c64*>(W + LA.y32);
     M.w32 = reinterpret_cast<c64*>(W + LA.w32);
-    M.ypart = reinterpret_cast<c64*>(W + LA.ypq);
     M.hpart = reinterpret_cast<c128*>(W + LA.hp);
     M.rn = reinterpret_cast<double*>(W + LA.rn);
     M.fn = reinterpret_cast<double*>(W + LA.fn);
@@ -1375,11 +790,11 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     T.pvf = B.pvf;
     T.pxv = B.pxv;
     T.hp = B.hp;
-    int rc = trd_reduce<float>(T, tab, st, status);
+    int rc = launch_trd_persist<float>(T, tab, B.bar, status, st);
     if (rc) return rc;
     if (a.ev_trd_done) cudaEventRecord(a.ev_trd_done, st);
     count_launch();
-    mix_cert_kernel<<<(nb + 63) / 64, 64, 0, st>>>(B, M, nb, a, status);
+    mix_cert_kernel<<<nb, 256, 0, st>>>(B, M, nb, a, status);
     int fb[MAXB];
     if (cudaMemcpyAsync(fb, M.fallback, sizeof(int) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -1394,7 +809,7 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
         count_launch();
         eig_all_kernel<<<dim3((nmax + 127) / 128, nb), 128, 0, st>>>(B, nb, a.shift, evals);
     }
-    // explicit Q = H_0 ... H_{n-2} by blocked WY accumulation, last panel first
+    // T factors of the reflector panels (blocked WY form of Q), then the refinement
     count_launch();
     upload_toff_kernel<<<1, 32, 0, st>>>(tab, M.toff);
     const int pmax = (nmax - 1 + QNB - 1) / QNB;
@@ -1402,36 +817,9 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
         count_launch();
         qt_factor_kernel<<<dim3(pmax, nb), 256, 0, st>>>(B, M);
     }
-    count_launch();
-    q_identity_kernel<<<dim3(256, nb), 256, 0, st>>>(B, M);
-    for (int p = pmax - 1; p >= 0; --p) {
-        const int m = nmax - p * QNB - 1;
-        const int tiles = (m + QT - 1) / QT;
-        count_launch();
-        q_w_kernel<<<dim3(tiles, nb), 256, 0, st>>>(B, M, p);
-        count_launch();
-        q_update_kernel<<<dim3(tiles, tiles, nb), 256, 0, st>>>(B, M, p);
-    }
     if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
-    // iterative refinement with FP64 residuals
-    count_launch();
-    ref_init_kernel<<<nb, 256, 0, st>>>(B, M, F);
-    const int tq = (nmax + 255) / 256;
-    const int T0 = tab.b[0].T;
-    for (int it = 0; it < REF_MAXIT; ++it) {
-        count_launch();
-        ref_qh_kernel<<<dim3(tq, tq, nb), 256, 0, st>>>(B, M, np);
-        count_launch();
-        ref_tri_kernel<<<(nb + 31) / 32, 32, 0, st>>>(B, M, nb, np);
-        count_launch();
-        ref_q_kernel<<<dim3((nmax + 7) / 8, nb), 256, 0, st>>>(B, M);
-        count_launch();
-        ref_hemv_kernel<<<dim3((unsigned)((long long)T0 * (T0 + 1) / 2), nb), 256, 0, st>>>(B, M);
-        count_launch();
-        ref_res_kernel<<<dim3((nmax + CH - 1) / CH, nb), CH, 0, st>>>(B, M, F, a.shift);
-        count_launch();
-        ref_conv_kernel<<<(nb + 63) / 64, 64, 0, st>>>(B, M, nb, it == REF_MAXIT - 1, status);
-    }
+    rc = launch_refine_persist(B, M, tab, F, a.shift, B.bar, status, st);
+    if (rc) return rc;
     count_launch();
     ref_out_kernel<<<nb, 256, 0, st>>>(B, M, a.eta, dtheta, n_kept);
     return cudaGetLastError() == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;

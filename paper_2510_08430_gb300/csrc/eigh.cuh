@@ -1,0 +1,93 @@
+// Shared definitions of the per-block eigensolver (eigh.cu) and of its persistent,
+// grid-synchronised kernels (eigh_persist.cu).
+#pragma once
+#include "internal.cuh"
+
+namespace nqs {
+
+constexpr int TB = 64;       // tile of the fused update + matvec
+constexpr int CH = 256;      // rows per CTA in the vector kernels
+constexpr int MAXCH = 512;   // max row chunks per block (n <= 131072)
+constexpr int DCH = 32;      // rows per unit of the tile-partial reductions
+constexpr int MAXDCH = MAXCH * (CH / DCH);
+constexpr int QL_MAXN = 12000;
+
+struct EBlk {
+    long long off;    // offset of the block in length-n_p arrays
+    long long soff;   // offset of S_b in the packed matrix array
+    long long yoff;   // offset of the block's matvec partials
+    int n;
+    int T;            // ceil(n / TB)
+    int orig;         // index of the block in the caller's order
+    int pad;
+};
+struct EBTab {
+    int nb;
+    EBlk b[MAXB];
+};
+struct HouseP {       // per-block scalars of the current reflector
+    c128 scale;       // 1 / (alpha - beta)
+    c128 tau;
+};
+struct BlkInfo {
+    double sigma_max;
+    double thr;
+    int n_dropped;
+    int n_kept;
+};
+
+struct SolveBufs {
+    const EBlk* tab;
+    unsigned* bar;        // grid-barrier state of the persistent kernels (2 words)
+    c128* S;
+    double *d, *e, *e2, *ev;
+    c128 *tau, *f, *v0, *v1, *w, *x, *z;
+    HouseP* hp;
+    BlkInfo* info;
+    double* pnorm;
+    c128 *pvf, *pxv, *ypart;
+    double* zmat;
+};
+
+// Views used by the Householder reduction in precision R (FP64 exact path,
+// FP32 preconditioner of the mixed path). f == nullptr skips the Q^H F update.
+template <typename R> struct TrdBufs {
+    const EBlk* tab;
+    cx<R>* A;
+    cx<R> *v0, *v1, *w, *x, *ypart;
+    c128* f;
+    double *d, *e, *e2, *pnorm;
+    c128 *tau, *pvf, *pxv;
+    HouseP* hp;
+};
+
+constexpr int QNB = 32;      // reflectors per panel of the blocked (WY) application of Q
+constexpr int REF_MAXIT = 30;
+constexpr double REF_TOL = 1e-14;
+
+struct MixBufs {
+    const EBlk* tab;
+    const c128* S;        // FP64 S (lower triangles), packed
+    c64* Sf;              // FP32 copy, reduced in place (reflectors in the upper rows)
+    c64* Tf;              // T factors: per block ceil((n-1)/QNB) panels x QNB x QNB
+    long long* toff;      // per slot offset into Tf
+    c64* pdot;            // panel dot products V_p^H y: [2][sum of row chunks][QNB]
+    double *d, *e;        // FP32-reduced tridiagonal (stored in FP64)
+    double *piv, *lmul;   // LDL^T of T + lambda I
+    c128 *x, *r;          // refinement iterate and residual (FP64)
+    c64 *r32, *y32, *w32; // FP32 work vectors
+    c128* hpart;          // FP64 Hermitian matvec partials (T^2 x 64 per block)
+    double* rn;           // per slot ||r||^2 partials [MAXCH]
+    double* fn;           // per slot ||F||^2
+    int* done;            // per slot converged flag
+    int* fallback;        // per slot: cutoff may drop an eigenvalue (needs the FP64 path)
+};
+
+// Persistent cooperative kernels (eigh_persist.cu). `bar` points to two zeroed words
+// of grid-barrier state; every grid-wide wait is bounded and reports NQS_ERR_TIMEOUT.
+template <typename R>
+int launch_trd_persist(const TrdBufs<R>& B, const EBTab& tab, unsigned* bar, DevStatus* status, cudaStream_t st);
+int launch_refine_persist(const SolveBufs& B, const MixBufs& M, const EBTab& tab, const c128* F, double shift,
+                          unsigned* bar, DevStatus* status, cudaStream_t st);
+
+}  // namespace nqs

@@ -1,0 +1,811 @@
+// Persistent, grid-synchronised kernels of the per-block solver (Sec. 2, block-layer
+// paragraph; S~_b = S_b + lambda I, dtheta_b = -eta pinv(S~_b) F_b):
+//
+//  trd_persist_kernel    Householder reduction Q^H S_b Q = T of every block, all columns
+//                        in one launch. Four phases per column, separated by grid
+//                        barriers:
+//                          A  rank-2 update of column i by reflector i-1 (w_{i-1} formed
+//                             on the fly from x_{i-1}, v_{i-1}), f <- H_{i-1}^H f, norm
+//                             partials of the sub-diagonal part of column i;
+//                          B  reflector scalars of column i (recomputed by every unit from
+//                             the norm partials) and v_i, stored in the upper part of row i;
+//                          C  trailing lower triangle: pending rank-2 update of step i-1 fused
+//                             with the Hermitian matvec y = A v_i (64 x 64 tiles);
+//                          D  x_i = tau_i y and the partials of x_i^H v_i.
+//  refine_persist_kernel Iterative refinement of the mixed-precision solve, all sweeps in
+//                        one launch: x += Q (T + lambda I)^{-1} Q^H r with Q applied in
+//                        blocked (WY) form, one panel of QNB reflectors per phase, then the
+//                        FP64 residual r = F - (S + lambda I) x and the convergence test.
+//
+// All CTAs of a cooperative launch are co-resident. Work of a phase is split into units
+// (row chunks or tiles of every active block) taken grid-stride. Data written in one
+// phase and read in a later one use plain global loads, never the read-only path.
+#include "eigh.cuh"
+
+namespace nqs {
+namespace {
+
+constexpr int PT = 256;                              // threads per CTA (== CH)
+constexpr unsigned long long BAR_NS = 2000000000ull; // budget of one grid-wide wait
+
+static_assert(PT == CH, "one thread per row of a chunk");
+static_assert(MAXB <= PT, "unit prefix holds one block per thread");
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier over all CTAs of the launch: bar[0] counts arrivals, bar[1] is the
+// generation. The last arriver resets the count and advances the generation. A wait
+// that exceeds BAR_NS records NQS_ERR_TIMEOUT and returns false; the caller returns.
+__device__ bool grid_sync(unsigned* bar, DevStatus* status, int where, int* ok_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = now_ns();
+            while (*gen == g) {
+                __nanosleep(64);
+                if (now_ns() - t0 > BAR_NS) {
+                    ok = 0;
+                    set_status(status, NQS_ERR_TIMEOUT, where, -1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *ok_s = ok;
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
+// pref[0..nb]: prefix of per-block unit counts (cnt(b) = 0 for a block idle in this
+// phase). Called by all threads of the CTA; returns the total.
+template <typename F>
+__device__ long long unit_prefix(int nb, F cnt, long long* pref, long long* wsum) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    long long v = (t < nb) ? cnt(t) : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    long long add = 0;
+    for (int k = 0; k < w; ++k) add += wsum[k];
+    if (t < nb) pref[t + 1] = v + add;
+    if (t == 0) pref[0] = 0;
+    __syncthreads();
+    return pref[nb];
+}
+
+// Block of unit u: the last b with pref[b] <= u (its count is then non-zero).
+__device__ __forceinline__ int unit_block(const long long* pref, int nb, long long u) {
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pref[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int tri_index(long long t, int* I, int* J) {
+    long long ii = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+    while (ii * (ii + 1) / 2 > t) --ii;
+    *I = (int)ii;
+    *J = (int)(t - ii * (ii + 1) / 2);
+    return 0;
+}
+
+// ------------------------------------------------------------------ reduction phases
+template <typename R> struct TrdSmem {
+    cx<R> sv[2][TB], svp[2][TB], swp[2][TB];
+    cx<R> p2buf[16][TB + 1];
+    cx<R> p1s[TB];
+};
+
+// A: column i (rows [i, n), chunk c) brought up to date by reflector i-1.
+template <typename R>
+__device__ void trd_phase_a(const TrdBufs<R>& B, int b, int i, int c, const cx<R>* vprev, double* shd, c128* shc) {
+    const EBlk blk = B.tab[b];
+    const int n = blk.n;
+    if (i >= 1) {
+        if (threadIdx.x < 32) {
+            const int nchp = (n - i + CH - 1) / CH;    // phase-B chunks of rows [i, n) at column i-1
+            const int nchd = (n - i + DCH - 1) / DCH;  // phase-D units of rows [i, n) at column i-1
+            c128 a = mk<double>(0.0, 0.0), g = a;
+            for (int k = threadIdx.x; k < nchd; k += 32) a = a + B.pxv[(long long)b * MAXDCH + k];
+            if (B.f)
+                for (int k = threadIdx.x; k < nchp; k += 32) g = g + B.pvf[(long long)b * MAXCH + k];
+            a = warp_sum(a);
+            g = warp_sum(g);
+            if (threadIdx.x == 0) {
+                const c128 tau = B.tau[blk.off + i - 1];
+                shc[0] = (-0.5) * (tau * a);  // w = x + alpha v
+                shc[1] = cconj(tau) * g;      // f <- f - g v
+            }
+        }
+        __syncthreads();
+    }
+    const long long r = (long long)i + (long long)c * CH + threadIdx.x;
+    cx<R>* A = B.A + blk.soff;
+    double nrm = 0.0;
+    if (r < n) {
+        cx<R> a = A[r * n + i];
+        if (i >= 1) {
+            const c128 alpha = shc[0];
+            const cx<R> vr = vprev[blk.off + r], vi = vprev[blk.off + i];
+            const cx<R> wr = ccast<R>(ccast<double>(B.x[blk.off + r]) + alpha * ccast<double>(vr));
+            const cx<R> wi = ccast<R>(ccast<double>(B.x[blk.off + i]) + alpha * ccast<double>(vi));
+            a = a - vr * cconj(wi) - wr * cconj(vi);
+            B.w[blk.off + r] = wr;
+            if (B.f) B.f[blk.off + r] = B.f[blk.off + r] - shc[1] * ccast<double>(vr);
+        }
+        if (r == i) {
+            a.im = R(0);
+            B.d[blk.off + i] = (double)a.re;
+        }
+        A[r * n + i] = a;
+        if (r >= i + 2) nrm = (double)cabs2(a);
+    }
+    nrm = block_sum(nrm, shd);
+    if (threadIdx.x == 0) B.pnorm[(long long)b * MAXCH + c] = nrm;
+}
+
+// B: reflector of column i (LAPACK-style: beta real, H^H [alpha; x] = [beta; 0]) and v_i
+// for rows [i+1, n), chunk c.
+template <typename R>
+__device__ void trd_phase_b(const TrdBufs<R>& B, int b, int i, int c, cx<R>* vcur, double* shd, c128* shc,
+                            DevStatus* status) {
+    const EBlk blk = B.tab[b];
+    const int n = blk.n;
+    cx<R>* A = B.A + blk.soff;
+    if (threadIdx.x < 32) {
+        const int nch = (n - i + CH - 1) / CH;  // chunks of phase A
+        double xn = 0.0;
+        for (int k = threadIdx.x; k < nch; k += 32) xn += B.pnorm[(long long)b * MAXCH + k];
+        xn = warp_sum(xn);
+        if (threadIdx.x == 0) {
+            const c128 alpha = ccast<double>(A[(long long)(i + 1) * n + i]);
+            double beta;
+            c128 tau, scale;
+            if (xn == 0.0 && alpha.im == 0.0) {
+                beta = alpha.re;
+                tau = mk<double>(0.0, 0.0);
+                scale = mk<double>(0.0, 0.0);
+            } else {
+                const double nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn);
+                beta = (alpha.re >= 0.0) ? -nrm : nrm;
+                tau = mk<double>((beta - alpha.re) / beta, -alpha.im / beta);
+                const c128 dnm = mk<double>(alpha.re - beta, alpha.im);
+                const double q = cabs2(dnm);
+                scale = mk<double>(dnm.re / q, -dnm.im / q);
+            }
+            shc[0] = scale;
+            if (c == 0) {
+                if (!isfinite(beta) || !finite_cx(tau) || !finite_cx(scale))
+                    set_status(status, NQS_ERR_NONFINITE, W_TRD, (long long)blk.orig * 1000000 + i);
+                B.e[blk.off + i] = beta;
+                B.e2[blk.off + i] = beta * beta;
+                B.tau[blk.off + i] = tau;
+            }
+        }
+    }
+    __syncthreads();
+    const cx<R> scale = ccast<R>(shc[0]);
+    const long long r = (long long)i + 1 + (long long)c * CH + threadIdx.x;
+    c128 vf = mk<double>(0.0, 0.0);
+    if (r < n) {
+        const cx<R> v = (r == i + 1) ? mk<R>(R(1), R(0)) : A[r * n + i] * scale;
+        vcur[blk.off + r] = v;
+        A[(long long)i * n + r] = v;
+        if (B.f) cmacc(vf, ccast<double>(v), B.f[blk.off + r]);
+    }
+    if (B.f) {
+        vf.re = block_sum(vf.re, shd);
+        vf.im = block_sum(vf.im, shd);
+        if (threadIdx.x == 0) B.pvf[(long long)b * MAXCH + c] = vf;
+    } else {
+        __syncthreads();
+    }
+}
+
+// C: tile t of the trailing region [i+1, n)^2 (lower triangle, absolute 64-tiles):
+//   A -= v_{i-1} w_{i-1}^H + w_{i-1} v_{i-1}^H  (pending, i >= 1);  y partials of A v_i.
+template <typename R>
+__device__ void trd_phase_c(const TrdBufs<R>& B, int b, int i, long long t, const cx<R>* vprev,
+                            const cx<R>* vcur, TrdSmem<R>& sm) {
+    const EBlk blk = B.tab[b];
+    const int n = blk.n;
+    const int R0 = i + 1;
+    const int T = blk.T;
+    const int J0 = R0 / TB;
+    int ii, jj;
+    tri_index(t, &ii, &jj);
+    const int I = J0 + ii, J = J0 + jj;
+    const bool pend = i >= 1;
+    const int tid = threadIdx.x;
+    const cx<R> zero = mk<R>(R(0), R(0));
+    if (tid < 2 * TB) {
+        const int which = tid / TB, q = tid % TB;
+        const int g = (which == 0 ? I : J) * TB + q;
+        cx<R> vv = zero, vp = zero, wp = zero;
+        if (g < n && g >= R0) {
+            vv = vcur[blk.off + g];
+            if (pend) {
+                vp = vprev[blk.off + g];
+                wp = B.w[blk.off + g];
+            }
+        }
+        sm.sv[which][q] = vv;
+        sm.svp[which][q] = vp;
+        sm.swp[which][q] = wp;
+    }
+    __syncthreads();
+    cx<R>* A = B.A + blk.soff;
+    const int tx = tid & 15, ty = tid >> 4;
+    cx<R> p1[4], p2[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) p1[a] = p2[a] = zero;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = ty + 16 * a;
+        const int rg = I * TB + r;
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) {
+            const int c = tx + 16 * bq;
+            const int cg = J * TB + c;
+            if (rg < n && cg < n && cg >= R0 && rg >= cg) {
+                const long long idx = (long long)rg * n + cg;
+                cx<R> x = A[idx];
+                if (pend) {
+                    x = x - sm.svp[0][r] * cconj(sm.swp[1][c]) - sm.swp[0][r] * cconj(sm.svp[1][c]);
+                    if (rg == cg) x.im = R(0);
+                    A[idx] = x;
+                }
+                cmac(p1[a], x, sm.sv[1][c]);
+                if (rg > cg) cmacc(p2[bq], x, sm.sv[0][r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            p1[a].re += __shfl_xor_sync(0xffffffffu, p1[a].re, o);
+            p1[a].im += __shfl_xor_sync(0xffffffffu, p1[a].im, o);
+        }
+        if (tx == 0) sm.p1s[ty + 16 * a] = p1[a];
+    }
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) sm.p2buf[ty][tx + 16 * bq] = p2[bq];
+    __syncthreads();
+    cx<R>* Y = B.ypart + blk.yoff;
+    if (tid < TB) {
+        cx<R> s2 = zero;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) s2 = s2 + sm.p2buf[k][tid];
+        if (I == J) {
+            Y[((long long)I * T + I) * TB + tid] = sm.p1s[tid] + s2;
+        } else {
+            Y[((long long)I * T + J) * TB + tid] = sm.p1s[tid];
+            Y[((long long)J * T + I) * TB + tid] = s2;
+        }
+    }
+    __syncthreads();
+}
+
+// D: y = sum of matvec partials, x_i = tau_i y, partials of x_i^H v_i, on rows
+// [i+1, n) in units of DCH rows; the tile partials of a row are split over the 8 warps.
+template <typename R>
+__device__ void trd_phase_d(const TrdBufs<R>& B, int b, int i, int c, const cx<R>* vcur, c128 (*red)[DCH]) {
+    const EBlk blk = B.tab[b];
+    const int n = blk.n;
+    const int t = threadIdx.x, lane = t & 31, g = t >> 5;
+    const long long r = (long long)i + 1 + (long long)c * DCH + lane;
+    const int T = blk.T, J0 = (i + 1) / TB;
+    c128 y = mk<double>(0.0, 0.0);
+    if (r < n) {
+        const int I = (int)(r / TB), rr = (int)(r % TB);
+        const cx<R>* Y = B.ypart + blk.yoff + (long long)I * T * TB + rr;
+#pragma unroll 4
+        for (int s = J0 + g; s < T; s += PT / 32) y = y + ccast<double>(Y[(long long)s * TB]);
+    }
+    red[g][lane] = y;
+    __syncthreads();
+    if (t < 32) {
+        c128 xv = mk<double>(0.0, 0.0);
+        if (r < n) {
+            c128 ys = red[0][lane];
+#pragma unroll
+            for (int k = 1; k < PT / 32; ++k) ys = ys + red[k][lane];
+            const c128 x = B.tau[blk.off + i] * ys;
+            B.x[blk.off + r] = ccast<R>(x);
+            cmacc(xv, x, ccast<double>(vcur[blk.off + r]));
+        }
+        xv = warp_sum(xv);
+        if (t == 0) B.pxv[(long long)b * MAXDCH + c] = xv;
+    }
+    __syncthreads();
+}
+
+template <typename R> struct TrdOcc { static constexpr int value = 2; };
+template <> struct TrdOcc<float> { static constexpr int value = 4; };  // FP32: 64 registers, 4 CTAs per SM
+
+template <typename R>
+__global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBufs<R> B, int nb, int nmax, unsigned* bar,
+                                                             DevStatus* status) {
+    __shared__ int sn[MAXB];
+    __shared__ long long pref[MAXB + 1];
+    __shared__ long long wsum[PT / 32];
+    __shared__ double shd[32];
+    __shared__ c128 shc[2];
+    __shared__ int ok_s;
+    __shared__ TrdSmem<R> sm;
+    __shared__ c128 red[PT / 32][DCH];
+    for (int b = threadIdx.x; b < nb; b += PT) sn[b] = B.tab[b].n;
+    __syncthreads();
+    for (int i = 0; i < nmax; ++i) {
+        cx<R>* vcur = (i & 1) ? B.v1 : B.v0;
+        const cx<R>* vprev = (i & 1) ? B.v0 : B.v1;
+        long long tot = unit_prefix(
+            nb, [&](int b) -> long long { return sn[b] - 1 >= i ? (sn[b] - i + CH - 1) / CH : 0; }, pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            trd_phase_a<R>(B, b, i, (int)(u - pref[b]), vprev, shd, shc);
+        }
+        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+        tot = unit_prefix(
+            nb, [&](int b) -> long long { return sn[b] - 2 >= i ? (sn[b] - i - 1 + CH - 1) / CH : 0; }, pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            trd_phase_b<R>(B, b, i, (int)(u - pref[b]), vcur, shd, shc, status);
+        }
+        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+        tot = unit_prefix(
+            nb,
+            [&](int b) -> long long {
+                if (sn[b] - 2 < i) return 0;
+                const long long T = (sn[b] + TB - 1) / TB, J0 = (i + 1) / TB;
+                return (T - J0) * (T - J0 + 1) / 2;
+            },
+            pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            trd_phase_c<R>(B, b, i, u - pref[b], vprev, vcur, sm);
+        }
+        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+        tot = unit_prefix(
+            nb, [&](int b) -> long long { return sn[b] - 2 >= i ? (sn[b] - i - 1 + DCH - 1) / DCH : 0; }, pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            trd_phase_d<R>(B, b, i, (int)(u - pref[b]), vcur, red);
+        }
+        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+    }
+}
+
+// ------------------------------------------------------------------ refinement phases
+struct RefSmem {
+    c64 uu[QNB];             // panel dot products V_p^H y of the block
+    c64 su[QNB];             // T_p u or T_p^H u
+    c64 ys[CH];              // chunk of the vector being transformed
+    c64 pp[PT / 32][QNB];    // per-part partial dot products
+    c128 red[PT / 32][DCH];  // per-warp partial matvec sums
+    c128 xs[2][TB];          // FP64 matvec
+    c128 p2buf[16][TB + 1];
+    c128 p1s[TB];
+};
+
+__device__ __forceinline__ int n_panels(int n) { return (n - 1 + QNB - 1) / QNB; }
+
+// On rows [r0, r0 + CH) of the block in slot b: vec -= V_p T_p^{(H)} (V_p^H vec), with
+// V_p^H vec summed from the chunk dot products of parity `par` (p < 0: no update); then
+// the chunk's dot products V_q^H vec for panel q into parity par ^ 1 (q < 0: none).
+// V_p = reflectors p*QNB .. p*QNB + QNB - 1, reflector k stored in row k's upper part
+// (v_k[k+1] = 1 stored explicitly); T_p upper triangular, row-major.
+__device__ void panel_apply(const MixBufs& M, const EBlk& blk, int b, long long cbase, long long totch, int c,
+                            int p, bool herm, int q, c64* vec, int par, RefSmem& sm) {
+    const int n = blk.n;
+    const c64* Sf = M.Sf + blk.soff;
+    const int t = threadIdx.x;
+    const int r = c * CH + t;
+    const int nch = (n + CH - 1) / CH;
+    c64 val = mk<float>(0.f, 0.f);
+    if (r < n) val = vec[blk.off + r];
+    if (p >= 0) {
+        {  // chunk dot products of the block, split over the 8 warps
+            const int j = t & 31, g = t >> 5;
+            c64 s = mk<float>(0.f, 0.f);
+            for (int k = g; k < nch; k += PT / 32) s = s + M.pdot[((long long)par * totch + cbase + k) * QNB + j];
+            sm.pp[g][j] = s;
+        }
+        __syncthreads();
+        if (t < QNB) {
+            c64 s = sm.pp[0][t];
+#pragma unroll
+            for (int k = 1; k < PT / 32; ++k) s = s + sm.pp[k][t];
+            sm.uu[t] = s;
+        }
+        __syncthreads();
+        const int i0 = p * QNB;
+        const int nbp = (n - 1 - i0) < QNB ? (n - 1 - i0) : QNB;
+        if (t < QNB) {
+            const c64* T = M.Tf + M.toff[b] + (long long)p * QNB * QNB;  // zero beyond nbp
+            c64 s = mk<float>(0.f, 0.f);
+            if (herm) {
+#pragma unroll 8
+                for (int k = 0; k < QNB; ++k)
+                    if (k <= t) cmacc(s, T[k * QNB + t], sm.uu[k]);  // (T^H u)_t
+            } else {
+#pragma unroll 8
+                for (int k = 0; k < QNB; ++k)
+                    if (k >= t) cmac(s, T[t * QNB + k], sm.uu[k]);   // (T u)_t
+            }
+            sm.su[t] = s;
+        }
+        __syncthreads();
+        if (r < n && r >= i0 + 1) {
+            c64 acc = mk<float>(0.f, 0.f);
+            const int jmax = (r - i0 - 1) < (nbp - 1) ? (r - i0 - 1) : (nbp - 1);  // r >= i0 + j + 1
+#pragma unroll 8
+            for (int j = 0; j < QNB; ++j)
+                if (j <= jmax) cmac(acc, Sf[(long long)(i0 + j) * n + r], sm.su[j]);
+            val = val - acc;
+            vec[blk.off + r] = val;
+        }
+    }
+    if (q >= 0) {
+        sm.ys[t] = val;
+        __syncthreads();
+        const int q0 = q * QNB;
+        const int nbq = (n - 1 - q0) < QNB ? (n - 1 - q0) : QNB;
+        const int j = t & 31, part = t >> 5;
+        c64 acc = mk<float>(0.f, 0.f);
+        if (j < nbq) {
+            const c64* v = Sf + (long long)(q0 + j) * n;
+            const int rlo = c * CH + part * 32;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const int rr = rlo + k;
+                if (rr < n && rr >= q0 + j + 1) cmacc(acc, v[rr], sm.ys[part * 32 + k]);
+            }
+        }
+        sm.pp[part][j] = acc;
+        __syncthreads();
+        if (t < QNB) {
+            c64 s = mk<float>(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < PT / 32; ++k) s = s + sm.pp[k][t];
+            M.pdot[((long long)(par ^ 1) * totch + cbase + c) * QNB + t] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// FP64 Hermitian matvec partials of S x over tile t of the lower triangle (64-tiles).
+__device__ void ref_hemv_tile(const MixBufs& M, const EBlk& blk, long long t, RefSmem& sm) {
+    const int n = blk.n;
+    const int T = blk.T;
+    int I, J;
+    tri_index(t, &I, &J);
+    const int tid = threadIdx.x;
+    if (tid < 2 * TB) {
+        const int which = tid / TB, q = tid % TB;
+        const int g = (which == 0 ? I : J) * TB + q;
+        sm.xs[which][q] = g < n ? M.x[blk.off + g] : mk<double>(0.0, 0.0);
+    }
+    __syncthreads();
+    const c128* S = M.S + blk.soff;
+    const int tx = tid & 15, ty = tid >> 4;
+    c128 p1[4], p2[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) p1[a] = p2[a] = mk<double>(0.0, 0.0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = ty + 16 * a;
+        const int rg = I * TB + r;
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) {
+            const int c = tx + 16 * bq;
+            const int cg = J * TB + c;
+            if (rg < n && cg < n && rg >= cg) {
+                c128 v = S[(long long)rg * n + cg];
+                if (rg == cg) v.im = 0.0;
+                cmac(p1[a], v, sm.xs[1][c]);
+                if (rg > cg) cmacc(p2[bq], v, sm.xs[0][r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            p1[a].re += __shfl_xor_sync(0xffffffffu, p1[a].re, o);
+            p1[a].im += __shfl_xor_sync(0xffffffffu, p1[a].im, o);
+        }
+        if (tx == 0) sm.p1s[ty + 16 * a] = p1[a];
+    }
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) sm.p2buf[ty][tx + 16 * bq] = p2[bq];
+    __syncthreads();
+    c128* Y = M.hpart + blk.yoff;
+    if (tid < TB) {
+        c128 s2 = mk<double>(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) s2 = s2 + sm.p2buf[k][tid];
+        if (I == J) {
+            Y[((long long)I * T + I) * TB + tid] = sm.p1s[tid] + s2;
+        } else {
+            Y[((long long)I * T + J) * TB + tid] = sm.p1s[tid];
+            Y[((long long)J * T + I) * TB + tid] = s2;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixBufs M, int nb, int pmaxall,
+                                                                const c128* F, double shift, unsigned* bar,
+                                                                DevStatus* status) {
+    __shared__ int sn[MAXB];
+    __shared__ long long cbase[MAXB + 1];  // prefix of row chunks over slots (pdot rows)
+    __shared__ int sdone[MAXB];
+    __shared__ long long pref[MAXB + 1];
+    __shared__ long long wsum[PT / 32];
+    __shared__ double shd[32];
+    __shared__ int ok_s;
+    __shared__ RefSmem sm;
+    const int tid = threadIdx.x;
+    for (int b = tid; b < nb; b += PT) sn[b] = B.tab[b].n;
+    __syncthreads();
+    if (tid == 0) {
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            cbase[b] = acc;
+            acc += (sn[b] + CH - 1) / CH;
+        }
+        cbase[nb] = acc;
+    }
+    __syncthreads();
+    const long long totch = cbase[nb];
+    auto chunks = [&](int b) -> long long { return (sn[b] + CH - 1) / CH; };
+
+    // x = 0, r = F, ||F||^2 (one CTA per block)
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const EBlk blk = B.tab[b];
+        double s = 0.0;
+        for (int k = tid; k < blk.n; k += PT) {
+            const c128 f = F[blk.off + k];
+            M.x[blk.off + k] = mk<double>(0.0, 0.0);
+            M.r[blk.off + k] = f;
+            M.r32[blk.off + k] = ccast<float>(f);
+            s += cabs2(f);
+        }
+        s = block_sum(s, shd);
+        if (tid == 0) M.fn[b] = s;
+    }
+    if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+    for (int b = tid; b < nb; b += PT) sdone[b] = (M.fn[b] == 0.0) ? 1 : 0;
+    __syncthreads();
+
+    for (int it = 0; it < REF_MAXIT; ++it) {
+        int open = 0;
+        for (int b = tid; b < nb; b += PT) open |= !sdone[b];
+        if (!__syncthreads_or(open)) break;
+
+        // ---- y = Q^H r: copy, then panels 0 .. pmax-1 with T^H
+        long long tot = unit_prefix(nb, [&](int b) -> long long { return sdone[b] ? 0 : chunks(b); }, pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            const int c = (int)(u - pref[b]);
+            const EBlk blk = B.tab[b];
+            const int r = c * CH + tid;
+            if (r < blk.n) M.y32[blk.off + r] = M.r32[blk.off + r];
+            __syncthreads();
+            panel_apply(M, blk, b, cbase[b], totch, c, -1, true, n_panels(blk.n) > 0 ? 0 : -1, M.y32, 1, sm);
+        }
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        for (int s = 0; s < pmaxall; ++s) {
+            tot = unit_prefix(
+                nb, [&](int b) -> long long { return (!sdone[b] && s < n_panels(sn[b])) ? chunks(b) : 0; }, pref,
+                wsum);
+            for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+                const int b = unit_block(pref, nb, u);
+                const EBlk blk = B.tab[b];
+                const int q = s + 1 < n_panels(blk.n) ? s + 1 : -1;
+                panel_apply(M, blk, b, cbase[b], totch, (int)(u - pref[b]), s, true, q, M.y32, s & 1, sm);
+            }
+            if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        }
+
+        // ---- w = (T + lambda I)^{-1} y by the LDL^T factors (one thread per block)
+        for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+            if (sdone[b] || tid != 0) continue;
+            const EBlk blk = B.tab[b];
+            const int n = blk.n;
+            const double* piv = M.piv + blk.off;
+            const double* l = M.lmul + blk.off;
+            const c64* y = M.y32 + blk.off;
+            c64* w = M.w32 + blk.off;
+            c128 uacc = mk<double>(0.0, 0.0);
+            for (int k = 0; k < n; ++k) {
+                const c128 yk = ccast<double>(y[k]);
+                uacc = (k == 0) ? yk : yk - l[k - 1] * uacc;
+                w[k] = ccast<float>(uacc);
+            }
+            c128 z = (1.0 / piv[n - 1]) * ccast<double>(w[n - 1]);
+            w[n - 1] = ccast<float>(z);
+            for (int k = n - 2; k >= 0; --k) {
+                z = (1.0 / piv[k]) * ccast<double>(w[k]) - l[k] * z;
+                w[k] = ccast<float>(z);
+            }
+        }
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+
+        // ---- x += Q w: panels pmax-1 .. 0 with T
+        tot = unit_prefix(nb, [&](int b) -> long long { return sdone[b] ? 0 : chunks(b); }, pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            const int c = (int)(u - pref[b]);
+            const EBlk blk = B.tab[b];
+            const int np_b = n_panels(blk.n);
+            panel_apply(M, blk, b, cbase[b], totch, c, -1, false, np_b - 1, M.w32, 1, sm);
+            const int r = c * CH + tid;
+            if (np_b == 0 && r < blk.n) M.x[blk.off + r] = M.x[blk.off + r] + ccast<double>(M.w32[blk.off + r]);
+        }
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        for (int s = 0; s < pmaxall; ++s) {
+            tot = unit_prefix(
+                nb, [&](int b) -> long long { return (!sdone[b] && s < n_panels(sn[b])) ? chunks(b) : 0; }, pref,
+                wsum);
+            for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+                const int b = unit_block(pref, nb, u);
+                const int c = (int)(u - pref[b]);
+                const EBlk blk = B.tab[b];
+                const int p = n_panels(blk.n) - 1 - s;
+                panel_apply(M, blk, b, cbase[b], totch, c, p, false, p - 1, M.w32, s & 1, sm);
+                const int r = c * CH + tid;
+                if (p == 0 && r < blk.n) M.x[blk.off + r] = M.x[blk.off + r] + ccast<double>(M.w32[blk.off + r]);
+            }
+            if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        }
+
+        // ---- FP64 residual r = F - (S + lambda I) x
+        tot = unit_prefix(
+            nb,
+            [&](int b) -> long long {
+                const long long T = (sn[b] + TB - 1) / TB;
+                return sdone[b] ? 0 : T * (T + 1) / 2;
+            },
+            pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            ref_hemv_tile(M, B.tab[b], u - pref[b], sm);
+        }
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        tot = unit_prefix(
+            nb, [&](int b) -> long long { return sdone[b] ? 0 : (sn[b] + DCH - 1) / DCH; }, pref, wsum);
+        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+            const int b = unit_block(pref, nb, u);
+            const int c = (int)(u - pref[b]);
+            const EBlk blk = B.tab[b];
+            const int n = blk.n;
+            const int lane = tid & 31, g = tid >> 5;
+            const int r = c * DCH + lane;
+            c128 y = mk<double>(0.0, 0.0);
+            if (r < n) {
+                const int T = blk.T, I = r / TB, rr = r % TB;
+                const c128* Y = M.hpart + blk.yoff + (long long)I * T * TB + rr;
+#pragma unroll 4
+                for (int k = g; k < T; k += PT / 32) y = y + Y[(long long)k * TB];
+            }
+            sm.red[g][lane] = y;
+            __syncthreads();
+            if (tid < 32) {
+                double s = 0.0;
+                if (r < n) {
+                    c128 ys = sm.red[0][lane];
+#pragma unroll
+                    for (int k = 1; k < PT / 32; ++k) ys = ys + sm.red[k][lane];
+                    const c128 x = M.x[blk.off + r];
+                    const c128 res = F[blk.off + r] - ys - shift * x;
+                    M.r[blk.off + r] = res;
+                    M.r32[blk.off + r] = ccast<float>(res);
+                    s = cabs2(res);
+                }
+                s = warp_sum(s);
+                if (tid == 0) M.rn[(long long)b * MAXDCH + c] = s;
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+
+        // ---- convergence (every CTA decides the same from the same partials)
+        for (int b = tid >> 5; b < nb; b += PT / 32) {  // one warp per block
+            if (sdone[b]) continue;
+            const int nch = (sn[b] + DCH - 1) / DCH;
+            double s = 0.0;
+            for (int c = tid & 31; c < nch; c += 32) s += M.rn[(long long)b * MAXDCH + c];
+            s = warp_sum(s);
+            if ((tid & 31) == 0) {
+                if (s <= REF_TOL * REF_TOL * M.fn[b]) {
+                    sdone[b] = 1;
+                } else if (blockIdx.x == 0) {
+                    if (!isfinite(s)) set_status(status, NQS_ERR_NONFINITE, W_SOLVE, B.tab[b].orig);
+                    else if (it == REF_MAXIT - 1) set_status(status, NQS_ERR_NOT_CONVERGED, W_SOLVE, B.tab[b].orig);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0)
+        for (int b = tid; b < nb; b += PT) M.done[b] = sdone[b];
+}
+
+int coop_grid(const void* fn, int smem, int cap_per_sm, int* grid) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NQS_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NQS_ERR_CUDA;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+        return NQS_ERR_UNSUPPORTED;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PT, smem) != cudaSuccess || per < 1)
+        return NQS_ERR_CUDA;
+    *grid = sms * (per < cap_per_sm ? per : cap_per_sm);
+    return NQS_OK;
+}
+
+}  // namespace
+
+template <typename R>
+int launch_trd_persist(const TrdBufs<R>& B, const EBTab& tab, unsigned* bar, DevStatus* status, cudaStream_t st) {
+    int nmax = 0;
+    for (int j = 0; j < tab.nb; ++j) nmax = tab.b[j].n > nmax ? tab.b[j].n : nmax;
+    int grid = 0;
+    const void* fn = (const void*)trd_persist_kernel<R>;
+    int rc = coop_grid(fn, 0, TrdOcc<R>::value, &grid);
+    if (rc) return rc;
+    if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return NQS_ERR_CUDA;
+    TrdBufs<R> Bc = B;
+    int nb = tab.nb;
+    void* args[] = {&Bc, &nb, &nmax, &bar, &status};
+    count_launch();
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PT), args, 0, st) == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
+}
+template int launch_trd_persist<float>(const TrdBufs<float>&, const EBTab&, unsigned*, DevStatus*, cudaStream_t);
+template int launch_trd_persist<double>(const TrdBufs<double>&, const EBTab&, unsigned*, DevStatus*, cudaStream_t);
+
+int launch_refine_persist(const SolveBufs& B, const MixBufs& M, const EBTab& tab, const c128* F, double shift,
+                          unsigned* bar, DevStatus* status, cudaStream_t st) {
+    int pmax = 0;
+    for (int j = 0; j < tab.nb; ++j) {
+        const int p = (tab.b[j].n - 1 + QNB - 1) / QNB;
+        pmax = p > pmax ? p : pmax;
+    }
+    int grid = 0;
+    const void* fn = (const void*)refine_persist_kernel;
+    int rc = coop_grid(fn, 0, 2, &grid);
+    if (rc) return rc;
+    if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return NQS_ERR_CUDA;
+    SolveBufs Bc = B;
+    MixBufs Mc = M;
+    int nb = tab.nb;
+    void* args[] = {&Bc, &Mc, &nb, &pmax, (void*)&F, &shift, &bar, &status};
+    count_launch();
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PT), args, 0, st) == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
+}
+
+}  // namespace nqs
