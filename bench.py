@@ -91,10 +91,39 @@ def gram_flops(w) -> tuple:
     return alg, full, issued
 
 
-def trd_flops(w) -> float:
+def trd_bytes(w, solver: str) -> float:
+    """Algorithmic DRAM bytes of one launch of the (unblocked, fused) Householder reduction
+    of all blocks: for every column, the lower triangle (diagonal included) of the trailing
+    m x m matrix is read once (Hermitian matvec) and written once (rank-2 update),
+    m = n_b - 1 .. 1, i.e. 2 * esize * (n_b - 1) n_b (n_b + 1) / 6 bytes per block; esize is
+    8 (complex64, mixed solver) or 16 (complex128, FP64 solver)."""
     import numpy as np
     nb = np.diff(w.block_off).astype(np.float64)
-    return float(np.sum(16.0 / 3.0 * nb ** 3))  # complex Hermitian Householder reduction
+    es = 8.0 if solver == "mixed" else 16.0
+    return float(np.sum(2.0 * es * (nb - 1.0) * nb * (nb + 1.0) / 6.0))
+
+
+def trd_traffic(w, solver: str):
+    """DRAM bytes per launch of the reduction kernel from the committed ncu summary, or None
+    when the summary is missing, is for another workload/solver, or the kernel source has
+    changed since it was taken (sha256 of eigh_persist.cu recorded in the summary)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"trd_persist_{w.name}.md")
+    src = os.path.join(ROOT, "paper_2510_08430_gb300", "csrc", "eigh_persist.cu")
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    rec = {}
+    for line in open(path):
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
+            rec[k.strip()] = v.strip().strip("`")
+    if rec.get("source_sha256") != sha or rec.get("solver") != solver or rec.get("n_s") != str(w.n_samples):
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -187,26 +216,6 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": d.get("hbm_gbs"), "bf16_tflops": d.get("bf16_tflops"),
                 "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
-
-
-def fp64_peak_tflops(torch) -> float:
-    """FP64 ALU peak of this GPU as measured by cuBLAS DGEMM (4096^3, best of 5)."""
-    n = 4096
-    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
-    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
-    a @ b
-    torch.cuda.synchronize()
-    best = 1e30
-    for _ in range(5):
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record()
-        a @ b
-        e.record()
-        e.synchronize()
-        best = min(best, s.elapsed_time(e) / 1e3)
-    del a, b
-    return 2.0 * n ** 3 / best / 1e12
 
 
 # ------------------------------------------------------------------ same-GPU comparisons
@@ -370,8 +379,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     alg, full, issued = gram_flops(w)
     gram_s = st_mean["gram"] / 1e3
     trd_s = st_mean["tridiagonal_reduction"] / 1e3
-    fp64_peak = fp64_peak_tflops(torch)
-    trd_tf = trd_flops(w) / trd_s / 1e12
+    hbm = peaks["hbm_gbs"]
+    trd_alg = trd_bytes(w, args.solver)
+    trd_gbs = trd_alg / trd_s / 1e9
+    traffic = trd_traffic(w, args.solver)
     bf16_peak = peaks["bf16_tflops"]
     gram_tf = alg / gram_s / 1e12
     line = {
@@ -380,13 +391,16 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
         "config": dict(workload_desc(w, args.solver), parallelism=("replicas" if world > 1 else "single")),
         "stage_ms": st_mean,
-        "roofline": {"kernel": "tridiagonal_reduction (trd_* kernel sequence, FP64)", "bound": "alu",
-                     "achieved": trd_tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": trd_tf / fp64_peak,
-                     "traffic": None,
-                     "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run",
-                     "algorithmic": "sum_b 16/3 n_b^3 flops per step"},
-        "roofline_gram": {"kernel": "gram_tc_kernel (tcgen05 BF16 hi+lo)", "bound": "tensor", "achieved": gram_tf,
-                          "peak": bf16_peak, "unit": "TFLOP/s", "frac": gram_tf / bf16_peak,
+        "roofline": {"kernel": ("trd_persist_kernel<float>" if args.solver == "mixed" else
+                                "trd_persist_kernel<double>") + " (Householder reduction of all blocks, one launch)",
+                     "bound": "hbm", "achieved": trd_gbs, "peak": hbm, "unit": "GB/s", "frac": trd_gbs / hbm,
+                     "traffic": traffic,
+                     "peak_source": f"hbm_gbs, {peaks['source']}",
+                     "algorithmic": "per block 2 * esize * (n_b-1) n_b (n_b+1) / 6 bytes (trailing lower triangle "
+                                    "read + written once per column)",
+                     "algorithmic_bytes": trd_alg, "ms_per_launch": st_mean["tridiagonal_reduction"]},
+        "roofline_gram": {"kernel": f"gram_tc_kernel (tcgen05, {w.precision})", "bound": "tensor",
+                          "achieved": gram_tf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": gram_tf / bf16_peak,
                           "peak_source": f"bf16_tflops burst, {peaks['source']}",
                           "issued_tflops": issued / gram_s / 1e12,
                           "algorithmic": "sum_b 4 n_b (n_b+1) N_s flops (unique lower triangle)",

@@ -265,8 +265,8 @@ NQS_API int sr_step(const nqs_model* m, const void* theta, const int8_t* configs
  * nqs_stage_timing(ws, 1) makes later sr_step calls on `ws` record CUDA events
  * on their stream at the stage boundaries: [0] Jacobian (parameter conversion,
  * forward, backward, O write), [1] local energies, [2] means/centring/force,
- * [3] block Gram, [4] Householder tridiagonal reduction, [5] eigenvalues, solve
- * and back-transform. nqs_stage_times synchronises on the last event and
+ * [3] block Gram (plus the solver's set-up copies), [4] Householder tridiagonal
+ * reduction (exactly its one kernel), [5] eigenvalues, solve and back-transform. nqs_stage_times synchronises on the last event and
  * returns the milliseconds of each stage of the most recent timed sr_step.
  * nqs_launch_count returns the number of kernels this library has launched in
  * the process (all threads). */

@@ -679,6 +679,7 @@ static int solve_fp64(SolveBufs& B, const EBTab& tab, int nmax, const c128* F, c
     T.pvf = B.pvf;
     T.pxv = B.pxv;
     T.hp = B.hp;
+    if (a.ev_trd_start) cudaEventRecord(a.ev_trd_start, st);
     int rc = launch_trd_persist<double>(T, tab, B.bar, status, st);
     if (rc) return rc;
     if (a.ev_trd_done) cudaEventRecord(a.ev_trd_done, st);
@@ -790,6 +791,7 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     T.pvf = B.pvf;
     T.pxv = B.pxv;
     T.hp = B.hp;
+    if (a.ev_trd_start) cudaEventRecord(a.ev_trd_start, st);
     int rc = launch_trd_persist<float>(T, tab, B.bar, status, st);
     if (rc) return rc;
     if (a.ev_trd_done) cudaEventRecord(a.ev_trd_done, st);

@@ -154,7 +154,7 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
     * ``chain10_rbm``      RBM alpha=1 on a 10-site Heisenberg chain, 512 samples, FP64.
     * ``j1j2_6x6_ffnn``    FFNN 36-64-64-1, 6x6 J1-J2 (J2=0.5), 4096 samples, FP32.
     * ``j1j2_10x10_ffnn5`` FFNN 100-64-64-64-64-1, 10x10 J1-J2, 16384 samples, BF16 split
-      (grouped error-free four-slice split: the element-wise two- and three-way
+      (grouped error-free five-slice split: the element-wise two- and three-way
       splits cannot reach a 1e-6 relative dtheta error on this workload).
     * ``j1j2_10x10_ffnn256`` FFNN 100-256-256-1, 10x10 J1-J2, 32768 samples.
     * ``batch8x8_<i>``     instance i (0..15) of the batched 8x8 workload.
