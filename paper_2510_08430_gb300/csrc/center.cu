@@ -179,10 +179,23 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 }
 
 // Grouped error-free split (O is c128, unchanged): for every parameter row and every
-// group of 16 samples, E = exponent of the group's max |Re|, |Im| of sqrt(w) dO; the
-// values t = x 2^-E (|t| < 1) are split into five BF16 slices s_i = rint(r 2^(8i+7))
-// 2^-(8i+7) (integers of at most 8 bits times a power of two), so that products of
-// slices of one group lie on a common grid and sums of 16 of them are exact.
+// group of 16 samples, E = exponent of the group's max |Re|, |Im| of sqrt(w) dO; each
+// value t = x 2^-E (|t| < 1) is rounded once to N = rint(t 2^39) and N is written in
+// balanced base 256, N = sum_q d_q 2^(8(4-q)) with |d_q| <= 128; slice q is the BF16
+// value d_q 2^-(8q+7) (an integer of at most 8 bits times a power of two, exact in
+// BF16). Products of slices of one group then lie on a common grid and sums of 16 of
+// them are exact in FP32.
+
+// Balanced base-256 digits of |N| < 2^39, most significant first.
+__device__ __forceinline__ void digits5(long long N, int (&d)[5]) {
+#pragma unroll
+    for (int q = 4; q >= 1; --q) {
+        const int lo = (int)(((N + 128) & 255) - 128);
+        d[q] = lo;
+        N = (N - lo) >> 8;
+    }
+    d[0] = (int)N;
+}
 constexpr int GROUP = 16;
 __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restrict__ O, long long ldo, long long ns,
                                                             const double* __restrict__ w,
@@ -234,20 +247,20 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         double mx = fmax(fabs(dr), fabs(di));
 #pragma unroll
         for (int o = GROUP / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o, GROUP));
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
+        // E with mx = m 2^E, m in [0.5, 1) (frexp convention), from the exponent bits
+        int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
+        ex = mx > 0.0 ? ex : 0;
         ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
         if ((s & (GROUP - 1)) == 0) gexp[(s / GROUP) * np + p] = (int8_t)ex;
-        const double inv = ldexp(1.0, -ex);
-        double tr = dr * inv, ti = di * inv;
+        const double sc = __longlong_as_double((long long)(1023 + 39 - ex) << 52);  // 2^(39 - E)
+        int dr5[5], di5[5];
+        digits5(__double2ll_rn(dr * sc), dr5);
+        digits5(__double2ll_rn(di * sc), di5);
+        const float qs[5] = {0x1p-7f, 0x1p-15f, 0x1p-23f, 0x1p-31f, 0x1p-39f};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            const double sc = ldexp(1.0, 8 * q + 7);
-            const double qr = rint(tr * sc) / sc, qi = rint(ti * sc) / sc;
-            pls[q][(2 * p) * ldk + s] = __double2bfloat16(qr);
-            pls[q][(2 * p + 1) * ldk + s] = __double2bfloat16(qi);
-            tr -= qr;
-            ti -= qi;
+            pls[q][(2 * p) * ldk + s] = __float2bfloat16_rn((float)dr5[q] * qs[q]);
+            pls[q][(2 * p + 1) * ldk + s] = __float2bfloat16_rn((float)di5[q] * qs[q]);
         }
     }
     fr = block_sum(fr, sh);

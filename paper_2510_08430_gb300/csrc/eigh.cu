@@ -23,7 +23,7 @@ namespace nqs {
 
 
 struct SolveLayout {
-    size_t tab, d, e, e2, tau, f, v0, v1, w, x, z, ev, hp, info, pnorm, pvf, pxv, ypart, zmat, total;
+    size_t tab, d, e, e2, tau, f, v0, v1, w, x, z, ev, hp, info, bcol, pvf, pxv, ypart, zmat, total;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -54,7 +54,7 @@ static SolveLayout solve_layout(const int64_t* off, int nb) {
     L.ev = take(8 * np);
     L.hp = take(sizeof(HouseP) * nb);
     L.info = take(sizeof(BlkInfo) * nb);
-    L.pnorm = take(8ull * nb * MAXCH);
+    L.bcol = take(16 * np);
     L.pvf = take(16ull * nb * MAXCH);
     L.pxv = take(16ull * nb * MAXDCH);
     L.ypart = take(16ull * ytot);
@@ -674,7 +674,7 @@ static int solve_fp64(SolveBufs& B, const EBTab& tab, int nmax, const c128* F, c
     T.d = B.d;
     T.e = B.e;
     T.e2 = B.e2;
-    T.pnorm = B.pnorm;
+    T.bcol = reinterpret_cast<decltype(T.bcol)>(B.bcol);
     T.tau = B.tau;
     T.pvf = B.pvf;
     T.pxv = B.pxv;
@@ -736,7 +736,7 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     B.z = reinterpret_cast<c128*>(W + L.z);
     B.hp = reinterpret_cast<HouseP*>(W + L.hp);
     B.info = reinterpret_cast<BlkInfo*>(W + L.info);
-    B.pnorm = reinterpret_cast<double*>(W + L.pnorm);
+    B.bcol = reinterpret_cast<c128*>(W + L.bcol);
     B.pvf = reinterpret_cast<c128*>(W + L.pvf);
     B.pxv = reinterpret_cast<c128*>(W + L.pxv);
     B.ypart = reinterpret_cast<c128*>(W + L.ypart);
@@ -786,7 +786,7 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     T.d = B.d;
     T.e = B.e;
     T.e2 = B.e2;
-    T.pnorm = B.pnorm;
+    T.bcol = reinterpret_cast<decltype(T.bcol)>(B.bcol);
     T.tau = B.tau;
     T.pvf = B.pvf;
     T.pxv = B.pxv;

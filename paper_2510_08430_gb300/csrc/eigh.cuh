@@ -44,7 +44,7 @@ struct SolveBufs {
     c128 *tau, *f, *v0, *v1, *w, *x, *z;
     HouseP* hp;
     BlkInfo* info;
-    double* pnorm;
+    c128* bcol;          // column buffer of the reduction (c64 view in the FP32 reduction)           // column-norm partials of the reduction [nb][MAXDCH][2]
     c128 *pvf, *pxv, *ypart;
     double* zmat;
 };
@@ -56,8 +56,9 @@ template <typename R> struct TrdBufs {
     cx<R>* A;
     cx<R> *v0, *v1, *w, *x, *ypart;
     c128* f;
-    double *d, *e, *e2, *pnorm;
+    double *d, *e, *e2;
     c128 *tau, *pvf, *pxv;
+    cx<R>* bcol;          // next column, updated except for the alpha part of the last reflector
     HouseP* hp;
 };
 

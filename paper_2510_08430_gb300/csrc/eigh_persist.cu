@@ -2,16 +2,16 @@
 // paragraph; S~_b = S_b + lambda I, dtheta_b = -eta pinv(S~_b) F_b):
 //
 //  trd_persist_kernel    Householder reduction Q^H S_b Q = T of every block, all columns
-//                        in one launch. Four phases per column, separated by grid
+//                        in one launch. Three phases per column j, separated by grid
 //                        barriers:
-//                          A  rank-2 update of column i by reflector i-1 (w_{i-1} formed
-//                             on the fly from x_{i-1}, v_{i-1}), f <- H_{i-1}^H f, norm
-//                             partials of the sub-diagonal part of column i;
-//                          B  reflector scalars of column i (recomputed by every unit from
-//                             the norm partials) and v_i, stored in the upper part of row i;
-//                          C  trailing lower triangle: pending rank-2 update of step i-1 fused
-//                             with the Hermitian matvec y = A v_i (64 x 64 tiles);
-//                          D  x_i = tau_i y and the partials of x_i^H v_i.
+//                          R  column j finalised (the alpha part of reflector j-1's update,
+//                             b - 2 Re(alpha) v), its sub-diagonal norm, reflector j and v_j
+//                             (stored in the upper part of row j), w_{j-1} = x_{j-1} + alpha v_{j-1};
+//                          C  trailing lower triangle: pending rank-2 update of reflector j-1
+//                             fused with the Hermitian matvec y = A v_j (64 x 64 tiles);
+//                          X  x_j = tau_j y, column j+1 updated by reflector j except for its
+//                             alpha part (b = a - v conj(x_{j+1}) - x), and the partials of
+//                             x_j^H v_j that give alpha_j.
 //  refine_persist_kernel Iterative refinement of the mixed-precision solve, all sweeps in
 //                        one launch: x += Q (T + lambda I)^{-1} Q^H r with Q applied in
 //                        blocked (WY) form, one panel of QNB reflectors per phase, then the
@@ -117,102 +117,97 @@ template <typename R> struct TrdSmem {
     cx<R> p1s[TB];
 };
 
-// A: column i (rows [i, n), chunk c) brought up to date by reflector i-1.
+// Between phase X of column j-1 and phase R of column j:
+//   bcol[r]  = column j (rows [j, n)) updated by reflector j-1 except for its alpha part,
+//              b = a - v_{j-1} conj(x_{j-1}[j]) - x_{j-1}; the full update is b - 2 Re(alpha) v;
+//   pxv[u]   = sum conj(x_r) v_r over DCH-row unit u of rows [j, n) (gives alpha_{j-1}).
+
+// Prologue: column 0 has nothing pending (b = a, x = v = 0). CTA unit c covers rows
+// [c CH, c CH + CH); warp w clears DCH-unit c (CH/DCH) + w.
 template <typename R>
-__device__ void trd_phase_a(const TrdBufs<R>& B, int b, int i, int c, const cx<R>* vprev, double* shd, c128* shc) {
+__device__ void trd_prologue(const TrdBufs<R>& B, int b, int c) {
     const EBlk blk = B.tab[b];
     const int n = blk.n;
-    if (i >= 1) {
-        if (threadIdx.x < 32) {
-            const int nchp = (n - i + CH - 1) / CH;    // phase-B chunks of rows [i, n) at column i-1
-            const int nchd = (n - i + DCH - 1) / DCH;  // phase-D units of rows [i, n) at column i-1
-            c128 a = mk<double>(0.0, 0.0), g = a;
-            for (int k = threadIdx.x; k < nchd; k += 32) a = a + B.pxv[(long long)b * MAXDCH + k];
-            if (B.f)
-                for (int k = threadIdx.x; k < nchp; k += 32) g = g + B.pvf[(long long)b * MAXCH + k];
-            a = warp_sum(a);
-            g = warp_sum(g);
-            if (threadIdx.x == 0) {
-                const c128 tau = B.tau[blk.off + i - 1];
-                shc[0] = (-0.5) * (tau * a);  // w = x + alpha v
-                shc[1] = cconj(tau) * g;      // f <- f - g v
-            }
-        }
-        __syncthreads();
-    }
-    const long long r = (long long)i + (long long)c * CH + threadIdx.x;
-    cx<R>* A = B.A + blk.soff;
-    double nrm = 0.0;
-    if (r < n) {
-        cx<R> a = A[r * n + i];
-        if (i >= 1) {
-            const c128 alpha = shc[0];
-            const cx<R> vr = vprev[blk.off + r], vi = vprev[blk.off + i];
-            const cx<R> wr = ccast<R>(ccast<double>(B.x[blk.off + r]) + alpha * ccast<double>(vr));
-            const cx<R> wi = ccast<R>(ccast<double>(B.x[blk.off + i]) + alpha * ccast<double>(vi));
-            a = a - vr * cconj(wi) - wr * cconj(vi);
-            B.w[blk.off + r] = wr;
-            if (B.f) B.f[blk.off + r] = B.f[blk.off + r] - shc[1] * ccast<double>(vr);
-        }
-        if (r == i) {
-            a.im = R(0);
-            B.d[blk.off + i] = (double)a.re;
-        }
-        A[r * n + i] = a;
-        if (r >= i + 2) nrm = (double)cabs2(a);
-    }
-    nrm = block_sum(nrm, shd);
-    if (threadIdx.x == 0) B.pnorm[(long long)b * MAXCH + c] = nrm;
+    const long long r = (long long)c * CH + threadIdx.x;
+    if (r < n) B.bcol[blk.off + r] = B.A[blk.soff + r * n];
+    if ((threadIdx.x & 31) == 0)
+        B.pxv[(long long)b * MAXDCH + (long long)c * (CH / DCH) + (threadIdx.x >> 5)] = mk<double>(0.0, 0.0);
 }
 
-// B: reflector of column i (LAPACK-style: beta real, H^H [alpha; x] = [beta; 0]) and v_i
-// for rows [i+1, n), chunk c.
+// R: column j on rows [j, n), chunk c (CH rows): finalise it, form reflector j
+// (LAPACK-style: beta real, H^H [alpha; x] = [beta; 0]) and v_j, and w_{j-1}. Every unit
+// computes the sub-diagonal norm of the final column itself (one pass over bcol).
 template <typename R>
-__device__ void trd_phase_b(const TrdBufs<R>& B, int b, int i, int c, cx<R>* vcur, double* shd, c128* shc,
-                            DevStatus* status) {
+__device__ void trd_phase_r(const TrdBufs<R>& B, int b, int j, int c, const cx<R>* vprev, cx<R>* vcur, double* shd,
+                            c128* shc, DevStatus* status) {
     const EBlk blk = B.tab[b];
     const int n = blk.n;
     cx<R>* A = B.A + blk.soff;
+    const cx<R>* bc = B.bcol + blk.off;
+    const cx<R>* vp = vprev + blk.off;
     if (threadIdx.x < 32) {
-        const int nch = (n - i + CH - 1) / CH;  // chunks of phase A
-        double xn = 0.0;
-        for (int k = threadIdx.x; k < nch; k += 32) xn += B.pnorm[(long long)b * MAXCH + k];
-        xn = warp_sum(xn);
+        const int K = (n - j + DCH - 1) / DCH;  // units of rows [j, n) of the previous phase
+        c128 p1 = mk<double>(0.0, 0.0);
+        for (int k = threadIdx.x; k < K; k += 32) p1 = p1 + B.pxv[(long long)b * MAXDCH + k];
+        p1 = warp_sum(p1);
         if (threadIdx.x == 0) {
-            const c128 alpha = ccast<double>(A[(long long)(i + 1) * n + i]);
-            double beta;
-            c128 tau, scale;
-            if (xn == 0.0 && alpha.im == 0.0) {
-                beta = alpha.re;
-                tau = mk<double>(0.0, 0.0);
-                scale = mk<double>(0.0, 0.0);
-            } else {
-                const double nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn);
-                beta = (alpha.re >= 0.0) ? -nrm : nrm;
-                tau = mk<double>((beta - alpha.re) / beta, -alpha.im / beta);
-                const c128 dnm = mk<double>(alpha.re - beta, alpha.im);
-                const double q = cabs2(dnm);
-                scale = mk<double>(dnm.re / q, -dnm.im / q);
-            }
-            shc[0] = scale;
-            if (c == 0) {
-                if (!isfinite(beta) || !finite_cx(tau) || !finite_cx(scale))
-                    set_status(status, NQS_ERR_NONFINITE, W_TRD, (long long)blk.orig * 1000000 + i);
-                B.e[blk.off + i] = beta;
-                B.e2[blk.off + i] = beta * beta;
-                B.tau[blk.off + i] = tau;
-            }
+            const c128 alpha = j >= 1 ? (-0.5) * (B.tau[blk.off + j - 1] * p1) : mk<double>(0.0, 0.0);
+            shc[0] = alpha;
         }
     }
     __syncthreads();
-    const cx<R> scale = ccast<R>(shc[0]);
-    const long long r = (long long)i + 1 + (long long)c * CH + threadIdx.x;
+    const c128 alpha = shc[0];
+    const R cc = (R)(2.0 * alpha.re);
+    const bool pend = j >= 1;
+    double xn = 0.0;
+    for (int r = j + 2 + threadIdx.x; r < n; r += PT) {
+        const cx<R> a = pend ? bc[r] - cc * vp[r] : bc[r];
+        xn += (double)cabs2(a);
+    }
+    xn = block_sum(xn, shd);
+    if (threadIdx.x == 0 && j <= n - 2) {
+        const c128 al = ccast<double>(pend ? bc[j + 1] - cc * vp[j + 1] : bc[j + 1]);
+        double beta;
+        c128 tau, scale;
+        if (xn == 0.0 && al.im == 0.0) {
+            beta = al.re;
+            tau = mk<double>(0.0, 0.0);
+            scale = mk<double>(0.0, 0.0);
+        } else {
+            const double nrm = sqrt(al.re * al.re + al.im * al.im + xn);
+            beta = (al.re >= 0.0) ? -nrm : nrm;
+            tau = mk<double>((beta - al.re) / beta, -al.im / beta);
+            const c128 dnm = mk<double>(al.re - beta, al.im);
+            const double q = cabs2(dnm);
+            scale = mk<double>(dnm.re / q, -dnm.im / q);
+        }
+        shc[1] = scale;
+        if (c == 0) {
+            if (!isfinite(beta) || !finite_cx(tau) || !finite_cx(scale))
+                set_status(status, NQS_ERR_NONFINITE, W_TRD, (long long)blk.orig * 1000000 + j);
+            B.e[blk.off + j] = beta;
+            B.e2[blk.off + j] = beta * beta;
+            B.tau[blk.off + j] = tau;
+        }
+    }
+    __syncthreads();
+    const long long r = (long long)j + (long long)c * CH + threadIdx.x;
     c128 vf = mk<double>(0.0, 0.0);
     if (r < n) {
-        const cx<R> v = (r == i + 1) ? mk<R>(R(1), R(0)) : A[r * n + i] * scale;
-        vcur[blk.off + r] = v;
-        A[(long long)i * n + r] = v;
-        if (B.f) cmacc(vf, ccast<double>(v), B.f[blk.off + r]);
+        cx<R> a = bc[r];
+        if (pend) {
+            const cx<R> vr = vp[r];
+            a = a - cc * vr;
+            B.w[blk.off + r] = ccast<R>(ccast<double>(B.x[blk.off + r]) + alpha * ccast<double>(vr));
+        }
+        if (r == j) {
+            B.d[blk.off + j] = (double)a.re;
+        } else if (j <= n - 2) {
+            const cx<R> v = (r == j + 1) ? mk<R>(R(1), R(0)) : a * ccast<R>(shc[1]);
+            vcur[blk.off + r] = v;
+            A[(long long)j * n + r] = v;
+            if (B.f) cmacc(vf, ccast<double>(v), B.f[blk.off + r]);
+        }
     }
     if (B.f) {
         vf.re = block_sum(vf.re, shd);
@@ -239,6 +234,19 @@ __device__ void trd_phase_c(const TrdBufs<R>& B, int b, int i, long long t, cons
     const bool pend = i >= 1;
     const int tid = threadIdx.x;
     const cx<R> zero = mk<R>(R(0), R(0));
+    cx<R>* A = B.A + blk.soff;
+    const int tx = tid & 15, ty = tid >> 4;
+    // the thread's 16 tile elements are loaded first: they depend on nothing staged below
+    cx<R> xv[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int rg = I * TB + ty + 16 * a;
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) {
+            const int cg = J * TB + tx + 16 * bq;
+            xv[a][bq] = (rg < n && cg < n && cg >= R0 && rg >= cg) ? A[(long long)rg * n + cg] : zero;
+        }
+    }
     if (tid < 2 * TB) {
         const int which = tid / TB, q = tid % TB;
         const int g = (which == 0 ? I : J) * TB + q;
@@ -255,8 +263,6 @@ __device__ void trd_phase_c(const TrdBufs<R>& B, int b, int i, long long t, cons
         sm.swp[which][q] = wp;
     }
     __syncthreads();
-    cx<R>* A = B.A + blk.soff;
-    const int tx = tid & 15, ty = tid >> 4;
     cx<R> p1[4], p2[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) p1[a] = p2[a] = zero;
@@ -269,12 +275,11 @@ __device__ void trd_phase_c(const TrdBufs<R>& B, int b, int i, long long t, cons
             const int c = tx + 16 * bq;
             const int cg = J * TB + c;
             if (rg < n && cg < n && cg >= R0 && rg >= cg) {
-                const long long idx = (long long)rg * n + cg;
-                cx<R> x = A[idx];
+                cx<R> x = xv[a][bq];
                 if (pend) {
                     x = x - sm.svp[0][r] * cconj(sm.swp[1][c]) - sm.swp[0][r] * cconj(sm.svp[1][c]);
                     if (rg == cg) x.im = R(0);
-                    A[idx] = x;
+                    A[(long long)rg * n + cg] = x;
                 }
                 cmac(p1[a], x, sm.sv[1][c]);
                 if (rg > cg) cmacc(p2[bq], x, sm.sv[0][r]);
@@ -308,42 +313,66 @@ __device__ void trd_phase_c(const TrdBufs<R>& B, int b, int i, long long t, cons
     __syncthreads();
 }
 
-// D: y = sum of matvec partials, x_i = tau_i y, partials of x_i^H v_i, on rows
-// [i+1, n) in units of DCH rows; the tile partials of a row are split over the 8 warps.
+// X: on rows [j+1, n) in units of DCH rows (the tile partials of a row split over the 8
+// warps): y = A v_j, x_j = tau_j y; column j+1 updated by reflector j except for the alpha
+// part, into bcol; f <- H_j^H f; the partials of x_j^H v_j.
 template <typename R>
-__device__ void trd_phase_d(const TrdBufs<R>& B, int b, int i, int c, const cx<R>* vcur, c128 (*red)[DCH]) {
+__device__ void trd_phase_x(const TrdBufs<R>& B, int b, int j, int c, const cx<R>* vcur, c128 (*red)[DCH],
+                            double* shd, c128* shc) {
     const EBlk blk = B.tab[b];
     const int n = blk.n;
     const int t = threadIdx.x, lane = t & 31, g = t >> 5;
-    const long long r = (long long)i + 1 + (long long)c * DCH + lane;
-    const int T = blk.T, J0 = (i + 1) / TB;
+    const long long r = (long long)j + 1 + (long long)c * DCH + lane;
+    const int T = blk.T, J0 = (j + 1) / TB;
+    const cx<R>* Yb = B.ypart + blk.yoff;
     c128 y = mk<double>(0.0, 0.0);
     if (r < n) {
         const int I = (int)(r / TB), rr = (int)(r % TB);
-        const cx<R>* Y = B.ypart + blk.yoff + (long long)I * T * TB + rr;
+        const cx<R>* Y = Yb + (long long)I * T * TB + rr;
 #pragma unroll 4
         for (int s = J0 + g; s < T; s += PT / 32) y = y + ccast<double>(Y[(long long)s * TB]);
     }
     red[g][lane] = y;
+    // y at row j+1 (needed by every row: x_{j+1} enters column j+1's update)
+    c128 y1 = mk<double>(0.0, 0.0);
+    {
+        const int I1 = (j + 1) / TB, rr1 = (j + 1) % TB;
+        for (int s = J0 + t; s < T; s += PT) y1 = y1 + ccast<double>(Yb[((long long)I1 * T + s) * TB + rr1]);
+    }
+    y1.re = block_sum(y1.re, shd);
+    y1.im = block_sum(y1.im, shd);
+    if (B.f && t < 32) {
+        const int K = (n - j + CH - 1) / CH;  // phase-R chunks of rows [j, n)
+        c128 pv = mk<double>(0.0, 0.0);
+        for (int k = t; k < K; k += 32) pv = pv + B.pvf[(long long)b * MAXCH + k];
+        pv = warp_sum(pv);
+        if (t == 0) shc[3] = cconj(B.tau[blk.off + j]) * pv;
+    }
     __syncthreads();
     if (t < 32) {
-        c128 xv = mk<double>(0.0, 0.0);
+        const c128 tau = B.tau[blk.off + j];
+        c128 p1 = mk<double>(0.0, 0.0);
         if (r < n) {
             c128 ys = red[0][lane];
 #pragma unroll
             for (int k = 1; k < PT / 32; ++k) ys = ys + red[k][lane];
-            const c128 x = B.tau[blk.off + i] * ys;
+            const c128 x = tau * ys;
+            const c128 x1 = tau * y1;
             B.x[blk.off + r] = ccast<R>(x);
-            cmacc(xv, x, ccast<double>(vcur[blk.off + r]));
+            const c128 v = ccast<double>(vcur[blk.off + r]);
+            cmacc(p1, x, v);
+            const cx<R>* A = B.A + blk.soff;
+            B.bcol[blk.off + r] = ccast<R>(ccast<double>(A[r * n + j + 1]) - v * cconj(x1) - x);
+            if (B.f) B.f[blk.off + r] = B.f[blk.off + r] - shc[3] * v;
         }
-        xv = warp_sum(xv);
-        if (t == 0) B.pxv[(long long)b * MAXDCH + c] = xv;
+        p1 = warp_sum(p1);
+        if (t == 0) B.pxv[(long long)b * MAXDCH + c] = p1;
     }
     __syncthreads();
 }
 
 template <typename R> struct TrdOcc { static constexpr int value = 2; };
-template <> struct TrdOcc<float> { static constexpr int value = 4; };  // FP32: 64 registers, 4 CTAs per SM
+template <> struct TrdOcc<float> { static constexpr int value = 3; };  // FP32: 3 CTAs per SM
 
 template <typename R>
 __global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBufs<R> B, int nb, int nmax, unsigned* bar,
@@ -352,47 +381,46 @@ __global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBu
     __shared__ long long pref[MAXB + 1];
     __shared__ long long wsum[PT / 32];
     __shared__ double shd[32];
-    __shared__ c128 shc[2];
+    __shared__ c128 shc[4];
     __shared__ int ok_s;
     __shared__ TrdSmem<R> sm;
     __shared__ c128 red[PT / 32][DCH];
     for (int b = threadIdx.x; b < nb; b += PT) sn[b] = B.tab[b].n;
     __syncthreads();
-    for (int i = 0; i < nmax; ++i) {
-        cx<R>* vcur = (i & 1) ? B.v1 : B.v0;
-        const cx<R>* vprev = (i & 1) ? B.v0 : B.v1;
-        long long tot = unit_prefix(
-            nb, [&](int b) -> long long { return sn[b] - 1 >= i ? (sn[b] - i + CH - 1) / CH : 0; }, pref, wsum);
-        for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
-            const int b = unit_block(pref, nb, u);
-            trd_phase_a<R>(B, b, i, (int)(u - pref[b]), vprev, shd, shc);
-        }
-        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+    long long tot = unit_prefix(nb, [&](int b) -> long long { return (sn[b] + CH - 1) / CH; }, pref, wsum);
+    for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
+        const int b = unit_block(pref, nb, u);
+        trd_prologue<R>(B, b, (int)(u - pref[b]));
+    }
+    if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+    for (int j = 0; j < nmax; ++j) {
+        cx<R>* vcur = (j & 1) ? B.v1 : B.v0;
+        const cx<R>* vprev = (j & 1) ? B.v0 : B.v1;
         tot = unit_prefix(
-            nb, [&](int b) -> long long { return sn[b] - 2 >= i ? (sn[b] - i - 1 + CH - 1) / CH : 0; }, pref, wsum);
+            nb, [&](int b) -> long long { return sn[b] - 1 >= j ? (sn[b] - j + CH - 1) / CH : 0; }, pref, wsum);
         for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
             const int b = unit_block(pref, nb, u);
-            trd_phase_b<R>(B, b, i, (int)(u - pref[b]), vcur, shd, shc, status);
+            trd_phase_r<R>(B, b, j, (int)(u - pref[b]), vprev, vcur, shd, shc, status);
         }
         if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
         tot = unit_prefix(
             nb,
             [&](int b) -> long long {
-                if (sn[b] - 2 < i) return 0;
-                const long long T = (sn[b] + TB - 1) / TB, J0 = (i + 1) / TB;
+                if (sn[b] - 2 < j) return 0;
+                const long long T = (sn[b] + TB - 1) / TB, J0 = (j + 1) / TB;
                 return (T - J0) * (T - J0 + 1) / 2;
             },
             pref, wsum);
         for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
             const int b = unit_block(pref, nb, u);
-            trd_phase_c<R>(B, b, i, u - pref[b], vprev, vcur, sm);
+            trd_phase_c<R>(B, b, j, u - pref[b], vprev, vcur, sm);
         }
         if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
         tot = unit_prefix(
-            nb, [&](int b) -> long long { return sn[b] - 2 >= i ? (sn[b] - i - 1 + DCH - 1) / DCH : 0; }, pref, wsum);
+            nb, [&](int b) -> long long { return sn[b] - 2 >= j ? (sn[b] - j - 1 + DCH - 1) / DCH : 0; }, pref, wsum);
         for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
             const int b = unit_block(pref, nb, u);
-            trd_phase_d<R>(B, b, i, (int)(u - pref[b]), vcur, red);
+            trd_phase_x<R>(B, b, j, (int)(u - pref[b]), vcur, red, shd, shc);
         }
         if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
     }
