@@ -261,6 +261,31 @@ NQS_API int sr_step(const nqs_model* m, const void* theta, const int8_t* configs
             int32_t precision, int32_t solver, void* dtheta_out, void* Emean_out, double* evals_out,
             int32_t* n_kept_out, int32_t flags, nqs_workspace* ws, void* stream);
 
+/* sr_step_batched -- n_inst independent SR steps in one call (batching of many
+ * instances). Instance i has its own model, n_s[i] samples, Hamiltonian and block
+ * partition; diag shift, cutoff, eta, precision and solver are shared. The Jacobians,
+ * local energies and centring run per instance; in the split precisions all blocks of
+ * all instances share one grouped tensor-core Gram launch (sample axis zero-padded to
+ * the largest n_s, which adds nothing), and every block goes through one eigensolver
+ * launch. Results equal n_inst separate sr_step calls up to rounding.
+ *   models[n_inst], hams[n_inst], n_s[n_inst], n_blocks[n_inst]: HOST arrays.
+ *   theta     : c128, the instances' parameter vectors concatenated.
+ *   configs   : int8, the instances' configuration arrays concatenated.
+ *   block_off : HOST int64, per instance its n_blocks[i] + 1 offsets (each starting at
+ *               0 and ending at that instance's n_p), concatenated.
+ *   dtheta_out: c128 [sum n_p], concatenated; Emean_out: c128 [n_inst].
+ *   evals_out : float64 [sum n_p] or NULL; n_kept_out: int32 [sum n_blocks] or NULL.
+ * At most 256 blocks over all instances (NQS_ERR_INVALID_ARG beyond). */
+NQS_API int sr_step_batched_workspace_size(int32_t n_inst, const nqs_model* models, const int64_t* n_s,
+                                   const nqs_hamiltonian* hams, const int64_t* block_off,
+                                   const int32_t* n_blocks, int32_t precision, size_t* bytes);
+NQS_API int sr_step_batched(int32_t n_inst, const nqs_model* models, const void* theta, const int8_t* configs,
+                    const int64_t* n_s, const nqs_hamiltonian* hams, const int64_t* block_off,
+                    const int32_t* n_blocks, double diag_shift, double cutoff, int32_t cutoff_mode,
+                    double eta, int32_t precision, int32_t solver, void* dtheta_out, void* Emean_out,
+                    double* evals_out, int32_t* n_kept_out, int32_t flags, nqs_workspace* ws,
+                    void* stream);
+
 /* ---- measurement hooks ----
  * nqs_stage_timing(ws, 1) makes later sr_step calls on `ws` record CUDA events
  * on their stream at the stage boundaries: [0] Jacobian (parameter conversion,

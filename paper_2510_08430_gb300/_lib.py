@@ -64,6 +64,8 @@ SIGNATURES = {
     "qgt_block_build_static": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P]),
     "qgt_block_solve": (C.c_int, [P, OFF, I32, P, D, D, I32, D, I32, P, P, P, P, P]),
     "sr_step": (C.c_int, [MP, P, P, I64, HP, OFF, I32, D, D, I32, D, I32, I32, P, P, P, P, I32, P, P]),
+    "sr_step_batched_workspace_size": (C.c_int, [I32, P, OFF, P, OFF, P, I32, SZ]),
+    "sr_step_batched": (C.c_int, [I32, P, P, P, OFF, P, OFF, P, D, D, I32, D, I32, I32, P, P, P, P, I32, P, P]),
     "nqs_stage_timing": (C.c_int, [P, I32]),
     "nqs_stage_times": (C.c_int, [P, C.POINTER(C.c_double), I32, C.POINTER(C.c_int32)]),
     "nqs_launch_count": (C.c_int64, []),

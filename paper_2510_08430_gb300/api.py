@@ -290,6 +290,38 @@ def sr_step(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamil
     return st.dtheta, st.emean, st.evals, st.n_kept
 
 
+def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float, cutoff: float, eta: float = 1.0,
+                    precision="split_bf16", cutoff_mode: int = 0, solver="mixed", want_evals: bool = False):
+    """Several independent SR steps in one call (one grouped Gram and one eigensolver launch).
+    Lists of per-instance Model, theta (c128 device), configs (int8 device), Hamiltonian and block
+    offsets. Returns (list of dtheta, Emean c128 [n_inst], evals or None, n_kept int32 [sum blocks])."""
+    lib = _lib.load()
+    n = len(models)
+    mods = (nqs_model * n)(*[m.c for m in models])
+    hs = (nqs_hamiltonian * n)(*[h.c for h in hams])
+    ns = (C.c_int64 * n)(*[int(x.shape[0]) for x in configs])
+    nbs = (C.c_int32 * n)(*[len(o) - 1 for o in block_offs])
+    offs = np.concatenate([np.asarray(o, dtype=np.int64) for o in block_offs])
+    off_c = (C.c_int64 * len(offs))(*offs.tolist())
+    p = _prec(precision)
+    sz = C.c_size_t(0)
+    check(lib.sr_step_batched_workspace_size(n, mods, ns, hs, off_c, nbs, p, C.byref(sz)))
+    dev = thetas[0].device
+    ws = Workspace(int(sz.value), device=dev)
+    th = torch.cat([t.reshape(-1) for t in thetas]).contiguous()
+    xc = torch.cat([x.reshape(-1) for x in configs]).contiguous()
+    np_tot = int(th.numel())
+    dth = torch.empty(np_tot, dtype=torch.complex128, device=dev)
+    em = torch.empty(n, dtype=torch.complex128, device=dev)
+    ev = torch.empty(np_tot, dtype=torch.float64, device=dev) if want_evals else None
+    nk = torch.empty(int(sum(len(o) - 1 for o in block_offs)), dtype=torch.int32, device=dev)
+    check(lib.sr_step_batched(n, mods, _ptr(th), _ptr(xc), ns, hs, off_c, nbs, float(diag_shift), float(cutoff),
+                              int(cutoff_mode), float(eta), p, _solver(solver), _ptr(dth), _ptr(em), _ptr(ev),
+                              _ptr(nk), NQS_SYNC, ws.h, _stream()))
+    sizes = [int(o[-1]) for o in block_offs]
+    return list(torch.split(dth, sizes)), em, ev, nk
+
+
 def launch_count() -> int:
     """Kernels launched by libnqs_sr in this process."""
     return int(_lib.load().nqs_launch_count())

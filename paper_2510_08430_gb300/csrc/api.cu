@@ -7,6 +7,7 @@
 #include <string>
 #include <new>
 #include <atomic>
+#include <cuda_bf16.h>
 #include "internal.cuh"
 
 using namespace nqs;
@@ -187,7 +188,7 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
     CK(launch_emean(eloc, w, ns, Emean, bb.e, status, st), "emean");
     const int nsp = nsplit_of(prec);
     CK(launch_center(prec, nsp, O, ldo, ns, np, w, bb.e, F, Omean, nsp ? bb.planes : nullptr, bb.ldk, bb.diag,
-                     bb.gexp, status, st),
+                     bb.gexp, np, status, st),
        "center");
     if (gram_event) CK(cudaEventRecord(gram_event, st), "event");
     GramTable* tab = new (std::nothrow) GramTable;
@@ -569,6 +570,236 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     return NQS_OK;
 }
 
+// ---------------------------------------------------------------- batched step
+// Several independent SR instances in one call (S9). Each instance's Jacobian, local
+// energies and centring run in turn in one reused region; the split-precision operands of
+// all instances go to one plane buffer (common sample stride, zero-padded: zeros add
+// nothing to the Gram), so all blocks of all instances share one grouped Gram launch and
+// one eigensolver launch.
+namespace {
+
+struct BatchPlan {
+    long long np_tot, ns_max, ldk, sq_tot;
+    int nb_tot;
+    int64_t off_all[MAXB + 1];
+    long long poff[MAXB + 1];  // parameter offset of each instance
+    long long soff[MAXB + 1];  // S offset of each instance
+    size_t inst_bytes;         // largest per-instance region
+};
+
+int plan_batch(int n_inst, const nqs_model* models, const int64_t* n_s, const nqs_hamiltonian* hams,
+               const int64_t* block_off, const int32_t* n_blocks, int prec, BatchPlan* bp) {
+    if (n_inst < 1 || n_inst > MAXB || !models || !n_s || !hams || !block_off || !n_blocks)
+        return fail(NQS_ERR_INVALID_ARG, "sr_step_batched: bad arguments");
+    if (check_prec(prec)) return NQS_ERR_INVALID_ARG;
+    bp->np_tot = 0;
+    bp->ns_max = 0;
+    bp->sq_tot = 0;
+    bp->nb_tot = 0;
+    bp->inst_bytes = 0;
+    bp->off_all[0] = 0;
+    const int64_t* off = block_off;
+    for (int i = 0; i < n_inst; ++i) {
+        ModelDesc md;
+        HamDesc hd;
+        if (n_s[i] < 1) return fail(NQS_ERR_INVALID_ARG, "instance %d: n_s < 1", i);
+        if (build_model_desc(&models[i], n_s[i], &md)) return fail(NQS_ERR_INVALID_ARG, "instance %d: bad model", i);
+        int rc = ham_desc(&hams[i], md.N, &hd);
+        if (rc) return rc;
+        rc = check_offsets(off, n_blocks[i], md.n_p);
+        if (rc) return rc;
+        if (bp->nb_tot + n_blocks[i] > MAXB)
+            return fail(NQS_ERR_INVALID_ARG, "more than %d blocks over all instances", MAXB);
+        bp->poff[i] = bp->np_tot;
+        bp->soff[i] = bp->sq_tot;
+        for (int b = 0; b < n_blocks[i]; ++b) {
+            const long long n = off[b + 1] - off[b];
+            bp->off_all[bp->nb_tot + b + 1] = bp->np_tot + off[b + 1];
+            bp->sq_tot += n * n;
+        }
+        bp->nb_tot += n_blocks[i];
+        bp->np_tot += md.n_p;
+        bp->ns_max = n_s[i] > bp->ns_max ? n_s[i] : bp->ns_max;
+        // per-instance region: model buffers, connections, O, local energies, centred e
+        Arena a = sizing_arena();
+        JacBufs jb, jbe;
+        ElocBufs eb;
+        plan_model(a, md, n_s[i], jac_prec(prec), &jb, true);
+        if (eloc_prec(prec) != jac_prec(prec)) plan_model(a, md, n_s[i], eloc_prec(prec), &jbe, false);
+        plan_eloc(a, n_s[i], hd.n_bonds, &eb);
+        a.take(csize(prec) * (size_t)md.n_p * (size_t)round_up(n_s[i], 32));
+        a.take(16 * (size_t)n_s[i]);
+        a.take(16 * (size_t)n_s[i]);
+        bp->inst_bytes = a.used > bp->inst_bytes ? a.used : bp->inst_bytes;
+        off += n_blocks[i] + 1;
+    }
+    bp->poff[n_inst] = bp->np_tot;
+    bp->soff[n_inst] = bp->sq_tot;
+    bp->ldk = round_up(bp->ns_max, 64);
+    return NQS_OK;
+}
+
+struct BatchBufs {
+    char* inst;
+    c128 *F, *S;
+    void* planes[5];
+    double* diag;
+    int8_t* gexp;
+};
+
+void plan_batch_bufs(Arena& a, const BatchPlan& bp, int prec, BatchBufs* bb) {
+    bb->inst = static_cast<char*>(a.take(bp.inst_bytes));
+    bb->F = static_cast<c128*>(a.take(16 * (size_t)bp.np_tot));
+    bb->S = static_cast<c128*>(a.take(16 * (size_t)bp.sq_tot));
+    const int nsp = nsplit_of(prec);
+    for (int q = 0; q < 5; ++q) bb->planes[q] = q < nsp ? a.take(2ull * 2 * bp.np_tot * bp.ldk) : nullptr;
+    bb->diag = nsp ? static_cast<double*>(a.take(8 * (size_t)bp.np_tot)) : nullptr;
+    bb->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(bp.ldk / 16) * bp.np_tot)) : nullptr;
+}
+
+}  // namespace
+
+extern "C" int sr_step_batched_workspace_size(int32_t n_inst, const nqs_model* models, const int64_t* n_s,
+                                              const nqs_hamiltonian* hams, const int64_t* block_off,
+                                              const int32_t* n_blocks, int32_t precision, size_t* bytes) {
+    if (!bytes) return fail(NQS_ERR_INVALID_ARG, "bytes is NULL");
+    BatchPlan* bp = new (std::nothrow) BatchPlan;
+    if (!bp) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    int rc = plan_batch(n_inst, models, n_s, hams, block_off, n_blocks, precision, bp);
+    if (!rc) {
+        Arena a = sizing_arena();
+        BatchBufs bb;
+        plan_batch_bufs(a, *bp, precision, &bb);
+        a.take(solve_workspace_bytes(bp->off_all, bp->nb_tot));
+        *bytes = a.used + STATUS_BYTES;
+    }
+    delete bp;
+    return rc;
+}
+
+extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const void* theta, const int8_t* configs,
+                               const int64_t* n_s, const nqs_hamiltonian* hams, const int64_t* block_off,
+                               const int32_t* n_blocks, double diag_shift, double cutoff, int32_t cutoff_mode,
+                               double eta, int32_t precision, int32_t solver, void* dtheta_out, void* Emean_out,
+                               double* evals_out, int32_t* n_kept_out, int32_t flags, nqs_workspace* ws,
+                               void* stream) {
+    if (!theta || !configs || !dtheta_out || !Emean_out) return fail(NQS_ERR_INVALID_ARG, "sr_step_batched: NULL");
+    BatchPlan* bp = new (std::nothrow) BatchPlan;
+    GramTable* tab = new (std::nothrow) GramTable;
+    if (!bp || !tab) {
+        delete bp;
+        delete tab;
+        return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    }
+    int rc = plan_batch(n_inst, models, n_s, hams, block_off, n_blocks, precision, bp);
+    if (rc) {
+        delete bp;
+        delete tab;
+        return rc;
+    }
+    Arena a = arena_of(ws);
+    BatchBufs bb;
+    plan_batch_bufs(a, *bp, precision, &bb);
+    Arena need = a;
+    need.take(solve_workspace_bytes(bp->off_all, bp->nb_tot));
+    rc = check_ws(ws, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* status = ws ? status_of(ws) : nullptr;
+    const int nsp = nsplit_of(precision);
+    const int rp = jac_prec(precision), re = eloc_prec(precision);
+    const char* th = static_cast<const char*>(theta);
+    const int8_t* xc = configs;
+    const int64_t* off = block_off;
+    tab->nb = 0;
+    tab->total_tiles = 0;
+    for (int i = 0; i < n_inst && !rc; ++i) {
+        ModelDesc md;
+        HamDesc hd;
+        build_model_desc(&models[i], n_s[i], &md);
+        ham_desc(&hams[i], md.N, &hd);
+        const long long ns = n_s[i];
+        Arena ia{bb.inst, bp->inst_bytes, 0};
+        JacBufs jb, jbe;
+        ElocBufs eb;
+        plan_model(ia, md, ns, rp, &jb, true);
+        if (re != rp) plan_model(ia, md, ns, re, &jbe, false);
+        else jbe = jb;
+        plan_eloc(ia, ns, hd.n_bonds, &eb);
+        const long long ldo = round_up(ns, 32);
+        void* O = ia.take(csize(precision) * (size_t)md.n_p * (size_t)ldo);
+        c128* eloc = static_cast<c128*>(ia.take(16 * (size_t)ns));
+        c128* e = static_cast<c128*>(ia.take(16 * (size_t)ns));
+        const long long po = bp->poff[i];
+        rc = run_model(md, rp, th, xc, ns, jb, st);
+        if (!rc) {
+            cudaError_t err = launch_backward(rp, md, jb.thR, jb.Z, ns, jb.G, st);
+            if (err == cudaSuccess) err = launch_jac_write(rp, md, jb.Z, jb.G, xc, ns, O, ldo, st);
+            if (err != cudaSuccess) rc = cuda_fail(err, "jacobian");
+        }
+        if (!rc && re != rp) rc = run_model(md, re, th, xc, ns, jbe, st);
+        if (!rc) rc = run_eloc(md, re, hd, xc, ns, jbe, eb, eloc, status, st);
+        if (!rc) {
+            cudaError_t err = launch_emean(eloc, nullptr, ns, static_cast<c128*>(Emean_out) + i, e, status, st);
+            void* pl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+            for (int q = 0; q < nsp; ++q)
+                pl[q] = static_cast<__nv_bfloat16*>(bb.planes[q]) + 2 * po * bp->ldk;
+            if (err == cudaSuccess)
+                err = launch_center(precision, nsp, O, ldo, ns, md.n_p, nullptr, e, bb.F + po, nullptr,
+                                    nsp ? pl : nullptr, bp->ldk, nsp ? bb.diag + po : nullptr,
+                                    nsp == 5 ? bb.gexp + po : nullptr, bp->np_tot, status, st);
+            if (err != cudaSuccess) rc = cuda_fail(err, "centring");
+        }
+        // the blocks of this instance in the shared Gram table (rows and S offsets global)
+        long long soff = bp->soff[i];
+        for (int b = 0; b < n_blocks[i] && !rc; ++b) {
+            const long long n = off[b + 1] - off[b];
+            const long long T = (n + 63) / 64;
+            GBlk& g = tab->b[tab->nb++];
+            g.row0 = po + off[b];
+            g.s_off = soff;
+            g.n = (int)n;
+            g.tiles = (int)(T * (T + 1) / 2);
+            g.tile0 = tab->total_tiles;
+            g.scale = 1.0 / (double)ns;
+            tab->total_tiles += T * (T + 1) / 2;
+            soff += n * n;
+        }
+        if (!rc && !nsp) {
+            // FP64/FP32: this instance's Gram now, while its centred O is alive
+            GramTable* ti = new (std::nothrow) GramTable;
+            if (!ti) {
+                rc = fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+            } else {
+                gram_table(off, n_blocks[i], 64, ti);
+                cudaError_t err = launch_gram_simt(precision, O, ldo, ns, nullptr, 1.0 / (double)ns, *ti,
+                                                   bb.S + bp->soff[i], st);
+                delete ti;
+                if (err != cudaSuccess) rc = cuda_fail(err, "gram");
+            }
+        }
+        th += 16 * (size_t)md.n_p;
+        xc += (size_t)ns * md.N;
+        off += n_blocks[i] + 1;
+    }
+    if (!rc && nsp) {
+        cudaError_t err = launch_gram_tc(nsp, bb.planes, bb.gexp, bp->np_tot, 2 * bp->np_tot, bp->ldk, bp->ldk, 0.0,
+                                         *tab, bb.S, status, st);
+        if (err == cudaSuccess) err = launch_set_diag(bb.S, *tab, bb.diag, st);
+        if (err == cudaErrorNotSupported) rc = fail(NQS_ERR_UNSUPPORTED, "tensor-core Gram needs an sm_103 device");
+        else if (err != cudaSuccess) rc = cuda_fail(err, "gram");
+    }
+    if (!rc) {
+        const int sv = solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver;
+        rc = run_solve(bb.S, bp->off_all, bp->nb_tot, bb.F, diag_shift, cutoff, cutoff_mode, eta, sv,
+                       static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a, status, st);
+    }
+    delete bp;
+    delete tab;
+    if (rc) return rc;
+    if (flags & NQS_SYNC) return nqs_sync_status(ws, stream);
+    return NQS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- build without a workspace
@@ -622,7 +853,7 @@ extern "C" int qgt_block_build_static(void* O, int64_t ldo, int64_t n_s, int64_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(launch_emean(static_cast<const c128*>(eloc), w, n_s, static_cast<c128*>(Emean_out), e, nullptr, st), "emean");
     CK(launch_center(precision, 0, O, ldo, n_s, n_p, w, e, static_cast<c128*>(F_out), static_cast<c128*>(Omean_out),
-                     nullptr, 0, nullptr, nullptr, nullptr, st),
+                     nullptr, 0, nullptr, nullptr, n_p, nullptr, st),
        "center");
     GramTable tab;  // host stack
     gram_table(block_off, n_blocks, 64, &tab);

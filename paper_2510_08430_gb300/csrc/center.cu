@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
                                                             __nv_bfloat16* __restrict__ pl2,
                                                             __nv_bfloat16* __restrict__ pl3,
                                                             __nv_bfloat16* __restrict__ pl4, int8_t* __restrict__ gexp,
-                                                            long long np, long long ldk, double* __restrict__ diag,
+                                                            long long gstride, long long ldk, double* __restrict__ diag,
                                                             DevStatus* status) {
     __shared__ double sh[32];
     const long long p = blockIdx.x;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
         ex = mx > 0.0 ? ex : 0;
         ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
-        if ((s & (GROUP - 1)) == 0) gexp[(s / GROUP) * np + p] = (int8_t)ex;
+        if ((s & (GROUP - 1)) == 0) gexp[(s / GROUP) * gstride + p] = (int8_t)ex;
         const double sc = __longlong_as_double((long long)(1023 + 39 - ex) << 52);  // 2^(39 - E)
         int dr5[5], di5[5];
         digits5(__double2ll_rn(dr * sc), dr5);
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
 
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          double* diag, int8_t* gexp, DevStatus* status, cudaStream_t st) {
+                          double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)np;
     if (nsplit == 5) {
@@ -285,7 +285,7 @@ cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long lon
         center_group_kernel<<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean,
                                                   (__nv_bfloat16*)planes[0], (__nv_bfloat16*)planes[1],
                                                   (__nv_bfloat16*)planes[2], (__nv_bfloat16*)planes[3],
-                                                  (__nv_bfloat16*)planes[4], gexp, np, ldk, diag, status);
+                                                  (__nv_bfloat16*)planes[4], gexp, gstride, ldk, diag, status);
     } else if (nsplit == 2 || nsplit == 3) {
         __nv_bfloat16* p0 = (__nv_bfloat16*)planes[0];
         __nv_bfloat16* p1 = (__nv_bfloat16*)planes[1];

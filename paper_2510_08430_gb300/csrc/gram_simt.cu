@@ -24,6 +24,7 @@ void gram_table(const int64_t* block_off, int nb, int tile_rows, GramTable* tab)
         tab->b[b].n = (int)n;
         tab->b[b].tiles = (int)(T * (T + 1) / 2);
         tab->b[b].tile0 = tiles;
+        tab->b[b].scale = 0.0;
         tiles += T * (T + 1) / 2;
         soff += n * n;
     }
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const cx<R>* __restrict_
         for (int c = 0; c < 4; ++c) {
             const int l = J * GT + tx + 16 * c;
             if (l >= n) continue;
-            S[blk.s_off + (long long)k * n + l] = mk<double>(scale * acc[a][c].re, scale * acc[a][c].im);
+            const double sc = blk.scale > 0.0 ? blk.scale : scale;
+            S[blk.s_off + (long long)k * n + l] = mk<double>(sc * acc[a][c].re, sc * acc[a][c].im);
         }
     }
 }

@@ -459,12 +459,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!ok) break;
             if (k < n) {
                 c128* Srow = S + blk.s_off + k * n;
+                const double sc = blk.scale > 0.0 ? blk.scale : scale;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const long long l = (long long)ti.J * (BM / 2) + 32 * half + 2 * j + cpar;
                     if (l < n)
-                        Srow[l] = mk<double>(scale * ((double)hre[j] + (double)lre[j]),
-                                             scale * ((double)him[j] + (double)lim[j]));
+                        Srow[l] = mk<double>(sc * ((double)hre[j] + (double)lre[j]),
+                                             sc * ((double)him[j] + (double)lim[j]));
                 }
             }
         }

@@ -72,7 +72,7 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 // error-free split with int8 exponents gexp[group][param], groups of 16 samples)
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          double* diag, int8_t* gexp, DevStatus* status, cudaStream_t st);
+                          double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st);
 
 // ---- Gram ----
 struct GBlk {                   // one QGT block of one instance
@@ -81,6 +81,7 @@ struct GBlk {                   // one QGT block of one instance
     int n;                      // block size
     int tiles;                  // lower-triangle tile count
     long long tile0;            // prefix of tiles over previous blocks
+    double scale;               // 1/N_s of the block's instance; 0: the launch's scale
 };
 struct GramTable {
     int nb;
