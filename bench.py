@@ -409,6 +409,27 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
     }
+    # the same step captured as one CUDA graph and replayed (launch overhead removed)
+    try:
+        step.capture(theta, x)
+        for _ in range(2):
+            step.replay()
+        torch.cuda.synchronize()
+        gt = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            step.replay()
+            e.record()
+            e.synchronize()
+            gt.append(s.elapsed_time(e) / 1e3)
+        step.ws.sync_status()
+        line["graph_replay"] = {"value": args.steps / sum(gt), "unit": "steps/s",
+                                "ms_per_step": 1e3 * sum(gt) / args.steps}
+    except Exception as exc:  # capture not possible here: report why, keep the direct timing
+        line["graph_replay"] = {"unavailable": str(exc)[:200]}
     if world == 1 and not args.no_fp64_compare:
         line["comparisons"] = compare_steps(nq, torch, np, w, model, ham, theta, x, dth_split, args.solver)
     if world == 1 and not args.no_cpu_baseline:

@@ -53,6 +53,8 @@ extern "C" {
 #define NQS_ERR_TIMEOUT       (-5) /* a device-side wait exhausted its iteration budget */
 #define NQS_ERR_NONFINITE     (-6) /* NaN/Inf found in O, E_loc, S or the solve */
 #define NQS_ERR_UNSUPPORTED   (-7) /* valid request this build does not implement */
+#define NQS_ERR_RETRY         (-8) /* NQS_GRAPH step whose mixed-solver certificate failed:
+                                      retake it without NQS_GRAPH (the FP64 path then runs) */
 
 /* ---- precision of the sample-space contractions (Jacobian, E_loc, Gram) ----
  * NQS_FP64        : everything in FP64; O is c128.
@@ -253,8 +255,16 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
  *   solver: NQS_SOLVE_FP64 or NQS_SOLVE_MIXED (see qgt_block_solve).
  *   dtheta_out: c128 [n_p]; Emean_out: c128 [1].
  *   evals_out / n_kept_out as in qgt_block_solve (may be NULL).
- *   flags: NQS_SYNC makes the call synchronise and return device status. */
+ *   flags: NQS_SYNC makes the call synchronise and return device status.
+ *          NQS_GRAPH makes the call capturable into a CUDA graph (stream capture):
+ *          nothing synchronises with the host. The mixed solver's certificate is then
+ *          checked on the device; when it fails the step's dtheta is not the definition's
+ *          and NQS_ERR_RETRY is recorded in the workspace status (nqs_sync_status). Stage
+ *          timing is not recorded, and NQS_SYNC must not be combined with it. The first
+ *          call on a device and shape should be made without capture (it sets kernel
+ *          attributes and loads kernels). */
 #define NQS_SYNC 1
+#define NQS_GRAPH 2
 NQS_API int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
             const nqs_hamiltonian* h, const int64_t* block_off, int32_t n_blocks,
             double diag_shift, double cutoff, int32_t cutoff_mode, double eta,

@@ -18,10 +18,12 @@ NQS_ERR_NOT_CONVERGED = -4
 NQS_ERR_TIMEOUT = -5
 NQS_ERR_NONFINITE = -6
 NQS_ERR_UNSUPPORTED = -7
+NQS_ERR_RETRY = -8
 
 NQS_FP64, NQS_FP32, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SPLIT_BF16_EXACT = 0, 1, 2, 3, 4
 NQS_RBM, NQS_FFNN = 0, 1
 NQS_SYNC = 1
+NQS_GRAPH = 2
 NQS_SOLVE_FP64, NQS_SOLVE_MIXED, NQS_SOLVE_MIXED_PSD = 0, 1, 2
 NQS_STATIC_MAX_SAMPLES = 65536
 

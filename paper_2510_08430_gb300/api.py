@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16_EXACT, NQS_SPLIT_BF16X3,
-                   NQS_SYNC, check, nqs_hamiltonian, nqs_model)
+                   NQS_GRAPH, NQS_SYNC, check, nqs_hamiltonian, nqs_model)
 
 PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3,
               "split_bf16_exact": NQS_SPLIT_BF16_EXACT}
@@ -271,12 +271,38 @@ class SRStep:
         check(_lib.load().nqs_stage_times(self.ws.h, ms, 8, C.byref(n)))
         return {self.STAGES[i]: ms[i] for i in range(n.value)}
 
-    def __call__(self, theta: torch.Tensor, configs: torch.Tensor, sync: bool = False):
+    def __call__(self, theta: torch.Tensor, configs: torch.Tensor, sync: bool = False, _flags: int = 0):
         lib = _lib.load()
         check(lib.sr_step(C.byref(self.model.c), _ptr(theta), _ptr(configs), self.n_s, C.byref(self.ham.c),
                           self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p, self.solver,
                           _ptr(self.dtheta), _ptr(self.emean), _ptr(self.evals), _ptr(self.n_kept),
-                          NQS_SYNC if sync else 0, self.ws.h, _stream()))
+                          (NQS_SYNC if sync else 0) | _flags, self.ws.h, _stream()))
+        return self.dtheta, self.emean
+
+    def capture(self, theta: torch.Tensor, configs: torch.Tensor) -> "torch.cuda.CUDAGraph":
+        """Capture one step into a CUDA graph over static copies of (theta, configs); replay()
+        then runs it for new inputs of the same shape. One uncaptured step runs first."""
+        self._g_theta = theta.detach().clone()
+        self._g_configs = configs.detach().clone()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self(self._g_theta, self._g_configs)
+        torch.cuda.current_stream().wait_stream(side)
+        self.ws.sync_status()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self(self._g_theta, self._g_configs, _flags=NQS_GRAPH)
+        self._graph = g
+        return g
+
+    def replay(self, theta: Optional[torch.Tensor] = None, configs: Optional[torch.Tensor] = None):
+        """Run the captured step (copying new inputs into its static buffers first)."""
+        if theta is not None:
+            self._g_theta.copy_(theta, non_blocking=True)
+        if configs is not None:
+            self._g_configs.copy_(configs, non_blocking=True)
+        self._graph.replay()
         return self.dtheta, self.emean
 
 

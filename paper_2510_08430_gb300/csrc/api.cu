@@ -212,7 +212,8 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
 
 int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, double cutoff, int mode,
               double eta, int solver, c128* dtheta, double* evals, int32_t* n_kept, Arena& a, DevStatus* status,
-              cudaStream_t st, cudaEvent_t trd_event = nullptr, cudaEvent_t trd_start = nullptr) {
+              cudaStream_t st, cudaEvent_t trd_event = nullptr, cudaEvent_t trd_start = nullptr,
+              bool graph = false) {
     if (solver != NQS_SOLVE_FP64 && solver != NQS_SOLVE_MIXED && solver != NQS_SOLVE_MIXED_PSD)
         return fail(NQS_ERR_INVALID_ARG, "unknown solver %d", solver);
     if (!(shift >= 0.0)) return fail(NQS_ERR_INVALID_ARG, "diag_shift must be >= 0");
@@ -221,7 +222,7 @@ int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, 
     const size_t need = solve_workspace_bytes(off, nb);
     void* work = a.take(need);
     SolveArgs sa{shift, cutoff, eta, mode, evals != nullptr, solver != NQS_SOLVE_FP64, solver == NQS_SOLVE_MIXED_PSD,
-                 trd_event, trd_start};
+                 trd_event, trd_start, graph};
     const int rc = launch_block_solve(S, off, nb, F, sa, dtheta, evals, n_kept, work, need, status, st);
     if (rc == NQS_ERR_UNSUPPORTED) return fail(rc, "block larger than the solver limit");
     if (rc != NQS_OK) return fail(rc, "block solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -538,7 +539,9 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DevStatus* status = status_of(ws);
     const int rp = jac_prec(precision), re = eloc_prec(precision);
-    const bool tm = ws->timing;
+    const bool graph = (flags & NQS_GRAPH) != 0;
+    if (graph && (flags & NQS_SYNC)) return fail(NQS_ERR_INVALID_ARG, "NQS_GRAPH cannot be combined with NQS_SYNC");
+    const bool tm = ws->timing && !graph;
     if (tm) CK(cudaEventRecord(ws->ev[0], st), "event");
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
@@ -560,7 +563,7 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     const int sv = solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver;
     rc = run_solve(S, block_off, n_blocks, F, diag_shift, cutoff, cutoff_mode, eta, sv,
                    static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a, status, st, tm ? ws->ev[5] : nullptr,
-                   tm ? ws->ev[4] : nullptr);
+                   tm ? ws->ev[4] : nullptr, graph);
     if (rc) return rc;
     if (tm) {
         CK(cudaEventRecord(ws->ev[6], st), "event");

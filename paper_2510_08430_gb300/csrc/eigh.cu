@@ -507,6 +507,12 @@ __global__ void __launch_bounds__(256) mix_cert_kernel(SolveBufs B, MixBufs M, i
     }
 }
 
+__global__ void retry_status_kernel(const int* __restrict__ fallback, int nb, DevStatus* status) {
+    int any = 0;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) any |= fallback[j];
+    if (__any_sync(0xffffffffu, any) && threadIdx.x == 0) set_status(status, NQS_ERR_RETRY, W_SOLVE, -1);
+}
+
 // T factor of each panel (forward, columnwise): T[j][j] = tau_j,
 // T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^H v_j), V = reflectors i0 .. i0+nbp-1.
 __global__ void __launch_bounds__(256) qt_factor_kernel(SolveBufs B, MixBufs M) {
@@ -797,15 +803,21 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     if (a.ev_trd_done) cudaEventRecord(a.ev_trd_done, st);
     count_launch();
     mix_cert_kernel<<<nb, 256, 0, st>>>(B, M, nb, a, status);
-    int fb[MAXB];
-    if (cudaMemcpyAsync(fb, M.fallback, sizeof(int) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return NQS_ERR_CUDA;
-    bool any_fb = false;
-    for (int j = 0; j < nb; ++j) any_fb = any_fb || fb[j];
-    if (any_fb) {
-        // some eigenvalue may be cut: take the exact FP64 path for every block
-        return solve_fp64(B, tab, nmax, F, a, dtheta, evals, n_kept, np, status, st);
+    if (a.no_host_sync) {
+        // capturable form: a failed certificate is reported, the caller retakes the step
+        count_launch();
+        retry_status_kernel<<<1, 32, 0, st>>>(M.fallback, nb, status);
+    } else {
+        int fb[MAXB];
+        if (cudaMemcpyAsync(fb, M.fallback, sizeof(int) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return NQS_ERR_CUDA;
+        bool any_fb = false;
+        for (int j = 0; j < nb; ++j) any_fb = any_fb || fb[j];
+        if (any_fb) {
+            // some eigenvalue may be cut: take the exact FP64 path for every block
+            return solve_fp64(B, tab, nmax, F, a, dtheta, evals, n_kept, np, status, st);
+        }
     }
     if (a.want_evals && evals) {
         count_launch();

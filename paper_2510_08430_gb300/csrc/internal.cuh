@@ -110,6 +110,7 @@ struct SolveArgs {
     bool psd;                   // S_b is a Gram matrix: sigma_min >= shift - 1e-6 sigma_max
     cudaEvent_t ev_trd_done;    // recorded after the tridiagonal reduction (or NULL)
     cudaEvent_t ev_trd_start;   // recorded just before the tridiagonal reduction (or NULL)
+    bool no_host_sync;          // capturable: the mixed certificate is checked on the device
 };
 size_t solve_workspace_bytes(const int64_t* block_off, int nb);
 int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
