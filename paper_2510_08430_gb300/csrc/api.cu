@@ -136,8 +136,11 @@ struct ElocBufs {
     int32_t *cnt, *cbond, *csamp;
     long long* off;
     c128* terms;
+    void* wdf;  // double-float (hi, lo) copy of the transposed weights (FP64 local energies)
 };
-void plan_eloc(Arena& a, long long ns, int nbonds, ElocBufs* b) {
+void plan_eloc(Arena& a, const ModelDesc& md, long long ns, int nbonds, ElocBufs* b) {
+    const long long we = model_wt_elems(md);
+    b->wdf = a.take(16 * (size_t)(we > 0 ? we : 1));
     const long long maxc = ns * nbonds;
     b->cnt = static_cast<int32_t*>(a.take(4 * ns));
     b->off = static_cast<long long*>(a.take(8 * (ns + 1)));
@@ -175,7 +178,8 @@ int run_eloc(const ModelDesc& md, int prec, const HamDesc& hd, const int8_t* x, 
     CK(launch_conn_count(x, ns, hd, eb.cnt, st), "conn_count");
     CK(launch_scan(eb.cnt, ns, eb.off, st), "scan");
     CK(launch_conn_fill(x, ns, hd, eb.off, eb.cbond, eb.csamp, st), "conn_fill");
-    CK(launch_conn_terms(prec, md, jb.thR, jb.wtR, jb.Z, jb.logpsi, x, hd, eb.cbond, eb.csamp, eb.off + ns,
+    if (prec == NQS_FP64) CK(launch_split_weights(md, jb.wtR, eb.wdf, st), "split_weights");
+    CK(launch_conn_terms(prec, md, jb.thR, jb.wtR, eb.wdf, jb.Z, jb.logpsi, x, hd, eb.cbond, eb.csamp, eb.off + ns,
                          ns * hd.n_bonds, eb.terms, st),
        "conn_terms");
     CK(launch_eloc_reduce(x, ns, hd, eb.off, eb.terms, eloc, status, st), "eloc_reduce");
@@ -341,7 +345,7 @@ int nqs_local_energy_workspace_size(const nqs_model* m, int64_t n_s, const nqs_h
     JacBufs jb;
     plan_model(a, md, n_s, eloc_prec(precision), &jb, false);
     ElocBufs eb;
-    plan_eloc(a, n_s, h->n_bonds, &eb);
+    plan_eloc(a, md, n_s, h->n_bonds, &eb);
     *bytes = a.used + STATUS_BYTES;
     return NQS_OK;
 }
@@ -372,7 +376,7 @@ static void plan_step(Arena& a, const ModelDesc& md, long long ns, int nbonds, c
     plan_model(a, md, ns, jac_prec(prec), jb, true);
     if (eloc_prec(prec) != jac_prec(prec)) plan_model(a, md, ns, eloc_prec(prec), jbe, false);
     else *jbe = *jb;
-    plan_eloc(a, ns, nbonds, eb);
+    plan_eloc(a, md, ns, nbonds, eb);
     plan_build(a, ns, md.n_p, prec, bb);
     *ldo = round_up(ns, 32);
     *O = a.take(csize(prec) * (size_t)md.n_p * (size_t)(*ldo));
@@ -440,7 +444,7 @@ int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* config
     const int rp = eloc_prec(precision);
     plan_model(a, md, n_s, rp, &jb, false);
     ElocBufs eb;
-    plan_eloc(a, n_s, hd.n_bonds, &eb);
+    plan_eloc(a, md, n_s, hd.n_bonds, &eb);
     rc = check_ws(ws, a);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -629,7 +633,7 @@ int plan_batch(int n_inst, const nqs_model* models, const int64_t* n_s, const nq
         ElocBufs eb;
         plan_model(a, md, n_s[i], jac_prec(prec), &jb, true);
         if (eloc_prec(prec) != jac_prec(prec)) plan_model(a, md, n_s[i], eloc_prec(prec), &jbe, false);
-        plan_eloc(a, n_s[i], hd.n_bonds, &eb);
+        plan_eloc(a, md, n_s[i], hd.n_bonds, &eb);
         a.take(csize(prec) * (size_t)md.n_p * (size_t)round_up(n_s[i], 32));
         a.take(16 * (size_t)n_s[i]);
         a.take(16 * (size_t)n_s[i]);
@@ -727,7 +731,7 @@ extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const vo
         plan_model(ia, md, ns, rp, &jb, true);
         if (re != rp) plan_model(ia, md, ns, re, &jbe, false);
         else jbe = jb;
-        plan_eloc(ia, ns, hd.n_bonds, &eb);
+        plan_eloc(ia, md, ns, hd.n_bonds, &eb);
         const long long ldo = round_up(ns, 32);
         void* O = ia.take(csize(precision) * (size_t)md.n_p * (size_t)ldo);
         c128* eloc = static_cast<c128*>(ia.take(16 * (size_t)ns));

@@ -230,6 +230,156 @@ __global__ void __launch_bounds__(256) conn_terms_kernel(ModelDesc md, const cx<
     }
 }
 
+// ------------------------------------------------------------------ double-float hidden layers
+// FP64 local energies of FFNNs: the hidden-layer products of the connected forwards run in
+// double-float arithmetic (each value an unevaluated sum hi + lo of two FP32 numbers; the
+// leading product is made exact with an FMA, cross terms and the TwoSum error go to the low
+// word), about 2^-48 relative, on the FP32 units; the first-layer update and ln cosh stay
+// in FP64. GB300's FP32 rate is some 64 times its FP64 rate.
+struct df2 {
+    float rh, ih, rl, il;  // re = rh + rl, im = ih + il
+};
+
+__device__ __forceinline__ df2 to_df(c128 z) {
+    df2 d;
+    d.rh = __double2float_rn(z.re);
+    d.rl = __double2float_rn(z.re - (double)d.rh);
+    d.ih = __double2float_rn(z.im);
+    d.il = __double2float_rn(z.im - (double)d.ih);
+    return d;
+}
+
+// (ah, al) += (xh + xl)(yh + yl). The intrinsics keep the compiler from contracting the
+// error-free transformations into FMAs.
+__device__ __forceinline__ void df_mac(float& ah, float& al, float xh, float xl, float yh, float yl) {
+    const float ph = __fmul_rn(xh, yh);
+    const float pl = fmaf(xh, yl, fmaf(xl, yh, fmaf(xh, yh, -ph)));
+    const float s = __fadd_rn(ah, ph);
+    const float bb = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(e, pl));
+}
+
+__global__ void split_weights_kernel(const c128* __restrict__ w, long long n, float4* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const df2 d = to_df(w[i]);
+        out[i] = make_float4(d.rh, d.ih, d.rl, d.il);
+    }
+}
+
+__global__ void __launch_bounds__(256) conn_terms_df_kernel(ModelDesc md, const c128* __restrict__ th,
+                                                             const c128* __restrict__ wt,
+                                                             const float4* __restrict__ wdf,
+                                                             const c128* __restrict__ Z,
+                                                             const c128* __restrict__ logpsi,
+                                                             const int8_t* __restrict__ x, HamDesc h,
+                                                             const int32_t* __restrict__ cbond,
+                                                             const int32_t* __restrict__ csamp,
+                                                             const long long* __restrict__ nconn_ptr, int TR,
+                                                             c128* __restrict__ terms) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = md.maxw;
+    df2* A = reinterpret_cast<df2*>(smem_raw);
+    df2* B = A + (size_t)TR * ld;
+    int* ssamp = reinterpret_cast<int*>(B + (size_t)TR * ld);
+    int* sbond = ssamp + TR;
+    double* sxi = reinterpret_cast<double*>(sbond + TR);
+    double* sxj = sxi + TR;
+    int* si = reinterpret_cast<int*>(sxj + TR);
+    int* sj = si + TR;
+    c128* lpn = reinterpret_cast<c128*>(((uintptr_t)(sj + TR) + 15) & ~(uintptr_t)15);
+    const long long nconn = *nconn_ptr;
+    const long long c0 = (long long)blockIdx.x * TR;
+    if (c0 >= nconn) return;
+    const int rows = (int)((nconn - c0) < TR ? (nconn - c0) : TR);
+    const int N = md.N;
+    for (int r = threadIdx.x; r < TR; r += blockDim.x) {
+        if (r < rows) {
+            const int s = csamp[c0 + r], b = cbond[c0 + r];
+            const int i = h.bond_ij[2 * b], j = h.bond_ij[2 * b + 1];
+            ssamp[r] = s;
+            sbond[r] = b;
+            si[r] = i;
+            sj[r] = j;
+            sxi[r] = (double)x[(long long)s * N + i];
+            sxj[r] = (double)x[(long long)s * N + j];
+        } else {
+            ssamp[r] = -1;
+            sbond[r] = 0;
+            si[r] = 0;
+            sj[r] = 0;
+            sxi[r] = 0.0;
+            sxj[r] = 0.0;
+        }
+    }
+    __syncthreads();
+    // first layer in FP64: z' = z - 2 x_i W[:, i] - 2 x_j W[:, j], then ln cosh
+    const int out0 = md.widths[1];
+    const c128* W0T = wt + md.wtoff[0];  // [N][out0]
+    for (int idx = threadIdx.x; idx < TR * out0; idx += blockDim.x) {
+        const int r = idx / out0, u = idx % out0;
+        c128 v = mk<double>(0.0, 0.0);
+        if (r < rows) {
+            const c128 z = Z[md.zoff[0] + (long long)ssamp[r] * out0 + u];
+            const c128 wi = W0T[(long long)si[r] * out0 + u];
+            const c128 wj = W0T[(long long)sj[r] * out0 + u];
+            const double ai = -2.0 * sxi[r], aj = -2.0 * sxj[r];
+            v = clncosh(mk<double>(z.re + ai * wi.re + aj * wj.re, z.im + ai * wi.im + aj * wj.im));
+        }
+        A[r * ld + u] = to_df(v);
+    }
+    __syncthreads();
+    for (int l = 1; l < md.L; ++l) {
+        const int out = md.widths[l + 1], in = md.widths[l];
+        const float4* W = wdf + md.wtoff[l];
+        const c128* bias = th + md.boff[l];
+        const int groups = (TR / 4) * out;
+        const bool last = l == md.L - 1;
+        for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+            const int rg = g / out, j = g % out;
+            df2 acc[4];
+            const df2 bj = to_df(bias[j]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = bj;
+            for (int k = 0; k < in; ++k) {
+                const float4 w = W[(long long)k * out + j];  // (re hi, im hi, re lo, im lo)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const df2 a = A[(4 * rg + q) * ld + k];
+                    df_mac(acc[q].rh, acc[q].rl, a.rh, a.rl, w.x, w.z);    // + a_re w_re
+                    df_mac(acc[q].rh, acc[q].rl, -a.ih, -a.il, w.y, w.w);  // - a_im w_im
+                    df_mac(acc[q].ih, acc[q].il, a.rh, a.rl, w.y, w.w);    // + a_re w_im
+                    df_mac(acc[q].ih, acc[q].il, a.ih, a.il, w.x, w.z);    // + a_im w_re
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = 4 * rg + q;
+                const c128 z = mk<double>((double)acc[q].rh + (double)acc[q].rl, (double)acc[q].ih + (double)acc[q].il);
+                if (last) {
+                    if (r < rows) lpn[r] = z;
+                } else {
+                    B[r * ld + j] = to_df(clncosh(z));
+                }
+            }
+        }
+        __syncthreads();
+        df2* t = A;
+        A = B;
+        B = t;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const c128 d = lpn[r] - logpsi[ssamp[r]];
+        const double m = exp(d.re);
+        double sn, cs;
+        sincos(d.im, &sn, &cs);
+        const double f = 2.0 * h.c * h.bond_J[sbond[r]] * (double)h.sign_rule;
+        terms[c0 + r] = mk<double>(f * m * cs, f * m * sn);
+    }
+}
+
 __global__ void eloc_reduce_kernel(const int8_t* __restrict__ x, long long ns, HamDesc h,
                                    const long long* __restrict__ off, const c128* __restrict__ terms,
                                    c128* __restrict__ eloc, DevStatus* status) {
@@ -305,10 +455,37 @@ static cudaError_t conn_terms_t(const ModelDesc& md, const void* thR, const void
     return cudaGetLastError();
 }
 
-cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, const void* wtR,
+cudaError_t launch_split_weights(const ModelDesc& md, const void* wtR, void* wdf, cudaStream_t st) {
+    const long long n = model_wt_elems(md);
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    split_weights_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(
+        (const c128*)wtR, n, (float4*)wdf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, const void* wtR, const void* wdf,
                               const void* Z, const c128* logpsi, const int8_t* x, const HamDesc& h,
                               const int32_t* conn_bond, const int32_t* conn_sample,
                               const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st) {
+    if (prec == NQS_FP64 && md.kind == NQS_FFNN && md.L >= 2 && wdf) {
+        if (max_conn <= 0) return cudaSuccess;
+        long long tr = 180000LL / (2LL * md.maxw * (long long)sizeof(c128));
+        tr = tr > 32 ? 32 : tr;
+        tr = (tr / 4) * 4;
+        const int TR = tr < 4 ? 4 : (int)tr;
+        const size_t smem = 2ull * TR * md.maxw * sizeof(c128) + (size_t)TR * (4 * sizeof(int) + 2 * sizeof(double)) +
+                            16 + (size_t)TR * sizeof(c128);
+        cudaError_t e =
+            cudaFuncSetAttribute(conn_terms_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const long long grid = (max_conn + TR - 1) / TR;
+        count_launch();
+        conn_terms_df_kernel<<<(unsigned)grid, 256, smem, st>>>(md, (const c128*)thR, (const c128*)wtR,
+                                                                 (const float4*)wdf, (const c128*)Z, logpsi, x, h,
+                                                                 conn_bond, conn_sample, nconn_ptr, TR, terms);
+        return cudaGetLastError();
+    }
     return prec == NQS_FP64
                ? conn_terms_t<double>(md, thR, wtR, Z, logpsi, x, h, conn_bond, conn_sample, nconn_ptr, max_conn,
                                       terms, st)

@@ -55,7 +55,9 @@ cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, i
 cudaError_t launch_scan(const int32_t* cnt, long long ns, long long* off, cudaStream_t st);
 cudaError_t launch_conn_fill(const int8_t* x, long long ns, const HamDesc& h, const long long* off,
                              int32_t* conn_bond, int32_t* conn_sample, cudaStream_t st);
-cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, const void* wtR,
+// (hi, lo) FP32 pairs of the transposed weights (c128) for the double-float connected forwards
+cudaError_t launch_split_weights(const ModelDesc& md, const void* wtR, void* wdf, cudaStream_t st);
+cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, const void* wtR, const void* wdf,
                               const void* Z, const c128* logpsi, const int8_t* x, const HamDesc& h,
                               const int32_t* conn_bond, const int32_t* conn_sample,
                               const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st);
