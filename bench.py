@@ -249,6 +249,15 @@ def compare_steps(nq, torch, np, w, model, ham, theta, x, dth, solver) -> dict:
     out[f"{w.precision}_{solver}solve (timed line)"] = {
         "dtheta_rel_err_vs_fp64_gpu": err(dth, d64),
         "dtheta_rel_err_vs_oracle": err(dth, ref) if ref is not None else None}
+    # the full QGT (one block of all n_p parameters; the paper's comparison) on the same inputs
+    full_off = np.array([0, int(w.block_off[-1])], dtype=np.int64)
+    stf = nq.SRStep(model, w.n_samples, ham, full_off, w.precision, w.diag_shift, w.cutoff, solver=solver)
+    tf, dfull = _timed_step(torch, stf, theta, x)
+    del stf
+    out[f"full_qgt_{w.precision}_{solver}solve"] = {
+        "seconds": tf, "blocks": [int(w.block_off[-1])],
+        "dtheta_rel_diff_vs_block": err(dfull, dth),
+        "note": "full-QGT update: a different method; it is not expected to equal the block-layer update"}
     for prec in ("fp32", "split_bf16", "split_bf16x3"):
         if prec == w.precision:
             continue

@@ -154,6 +154,14 @@ NQS_API int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* co
                  int32_t precision, void* logpsi_out, void* O_out, int64_t ldo,
                  nqs_workspace* ws, void* stream);
 
+/* nqs_vjp -- vector-Jacobian product of ln psi: out[k] = sum_s conj(O[k*ldo + s]) g[s],
+ * the gradient a reverse-mode framework propagates to theta for an upstream gradient g of
+ * ln psi (ln psi is holomorphic in theta). O as written by nqs_jacobian with the same
+ * precision (c64 for NQS_FP32, c128 otherwise); g: c128 [n_s]; out: c128 [n_p]. FP64
+ * accumulation. No workspace. */
+NQS_API int nqs_vjp(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t precision, const void* g,
+            void* out, void* stream);
+
 /* nqs_local_energy -- E_loc(x_s) (Eq. 1) for the Hamiltonian h:
  *   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign_rule psi(x^{ij})/psi(x) ],
  * x^{ij} = x with spins i and j flipped; connected configurations are visited in

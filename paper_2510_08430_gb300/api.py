@@ -140,6 +140,36 @@ def nqs_jacobian(model: Model, theta: torch.Tensor, configs: torch.Tensor, preci
     return logpsi, O
 
 
+class NQSLogPsi(torch.autograd.Function):
+    """ln psi(configs; theta) with the hand-written per-sample backward of the library:
+    forward runs nqs_jacobian (ln psi and the Jacobian O in one pass); backward returns
+    sum_s conj(O_sk) g_s (nqs_vjp), the gradient of a holomorphic function in PyTorch's
+    conjugate-Wirtinger convention."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, model: "Model", configs: torch.Tensor, precision: str = "fp64"):
+        logpsi, O = nqs_jacobian(model, theta.detach(), configs, precision)
+        ctx.save_for_backward(O)
+        ctx.precision = precision
+        ctx.n_s = int(configs.shape[0])
+        return logpsi
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        (O,) = ctx.saved_tensors
+        lib = _lib.load()
+        g = grad_out.to(torch.complex128).contiguous()
+        out = torch.empty(O.shape[0], dtype=torch.complex128, device=O.device)
+        check(lib.nqs_vjp(_ptr(O), int(O.shape[1]), ctx.n_s, int(O.shape[0]), _prec(ctx.precision), _ptr(g),
+                          _ptr(out), _stream()))
+        return out, None, None, None
+
+
+def log_psi(model: "Model", theta: torch.Tensor, configs: torch.Tensor, precision: str = "fp64") -> torch.Tensor:
+    """Differentiable ln psi (see NQSLogPsi)."""
+    return NQSLogPsi.apply(theta, model, configs, precision)
+
+
 def nqs_local_energy(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian,
                      precision="fp64", ws: Optional[Workspace] = None, sync: bool = True) -> torch.Tensor:
     lib = _lib.load()

@@ -430,6 +430,16 @@ int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, i
     return NQS_OK;
 }
 
+int nqs_vjp(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t precision, const void* g, void* out,
+            void* stream) {
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (!O || !g || !out || n_s < 1 || n_p < 1 || ldo < n_s) return fail(NQS_ERR_INVALID_ARG, "nqs_vjp: bad arguments");
+    CK(launch_vjp(jac_prec(precision), O, ldo, n_s, n_p, static_cast<const c128*>(g), static_cast<c128*>(out),
+                  static_cast<cudaStream_t>(stream)),
+       "vjp");
+    return NQS_OK;
+}
+
 int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
                      const nqs_hamiltonian* h, int32_t precision, void* eloc_out, nqs_workspace* ws, void* stream) {
     ModelDesc md;

@@ -275,6 +275,31 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
     }
 }
 
+// out[k] = sum_s conj(O[k][s]) g[s] (vector-Jacobian product of ln psi, FP64 accumulation).
+template <typename R>
+__global__ void __launch_bounds__(256) vjp_kernel(const cx<R>* __restrict__ O, long long ldo, long long ns,
+                                                   const c128* __restrict__ g, c128* __restrict__ out) {
+    __shared__ double sh[32];
+    const long long p = blockIdx.x;
+    const cx<R>* row = O + p * ldo;
+    c128 acc = mk<double>(0.0, 0.0);
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) cmacc(acc, ccast<double>(row[s]), g[s]);
+    acc.re = block_sum(acc.re, sh);
+    acc.im = block_sum(acc.im, sh);
+    if (threadIdx.x == 0) out[p] = acc;
+}
+
+cudaError_t launch_vjp(int prec, const void* O, long long ldo, long long ns, long long np, const c128* g, c128* out,
+                       cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    count_launch();
+    if (prec == NQS_FP32)
+        vjp_kernel<float><<<(unsigned)np, 256, 0, st>>>((const c64*)O, ldo, ns, g, out);
+    else
+        vjp_kernel<double><<<(unsigned)np, 256, 0, st>>>((const c128*)O, ldo, ns, g, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
                           double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st) {
