@@ -223,6 +223,26 @@ NQS_API int qgt_block_build_static(void* O, int64_t ldo, int64_t n_s, int64_t n_
                            int32_t precision, void* S_packed, void* F_out, void* Omean_out,
                            void* Emean_out, void* stream);
 
+/* ---- sample sharding ----
+ * A step over N samples split into shards (one per rank, or several on one GPU) needs
+ * two exchanges: the global means before centring, and the sum of the shards' S and F.
+ * nqs_shard_sums -- osum_out[k] = sum_{s in shard} O[k*ldo + s] (c128 [n_p]) and
+ *   esum_out[0] = sum_{s in shard} E_loc(s) (c128 [1]); FP64 accumulation. Summed over
+ *   all shards and divided by N they give <O> and <E>. No workspace.
+ * qgt_block_build_shard -- a shard's part of qgt_block_build: with the GLOBAL means
+ *   Omean_in (c128 [n_p]) and Emean_in (c128 [1]) and weight = 1/N for every sample,
+ *     S_packed = weight sum_{s in shard} dO_s^H dO_s (lower triangles, as qgt_block_build),
+ *     F_out    = weight sum_{s in shard} conj(dO_s) e_s,
+ *   dO = O - <O>, e = E_loc - <E>. The sums over all shards of S_packed and F_out are
+ *   qgt_block_build's S and F of all N samples. O is overwritten with dO in the
+ *   FP64/FP32 modes (as qgt_block_build). Workspace: qgt_block_build_workspace_size. */
+NQS_API int nqs_shard_sums(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t precision,
+                   const void* eloc, void* osum_out, void* esum_out, void* stream);
+NQS_API int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, double weight,
+                          const int64_t* block_off, int32_t n_blocks, const void* eloc,
+                          const void* Omean_in, const void* Emean_in, int32_t precision,
+                          void* S_packed, void* F_out, nqs_workspace* ws, void* stream);
+
 /* ---- per-block solver ----
  * NQS_SOLVE_FP64 : the Householder reduction, eigenvalues and solve all in FP64.
  * NQS_SOLVE_MIXED: the O(n^3) reduction runs in FP32 on a copy of S_b (FP64 units run

@@ -508,6 +508,56 @@ int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const double
                      static_cast<c128*>(Emean_out), bb, status_of(ws), static_cast<cudaStream_t>(stream));
 }
 
+int nqs_shard_sums(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t precision, const void* eloc,
+                   void* osum_out, void* esum_out, void* stream) {
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (!O || !eloc || !osum_out || !esum_out || n_s < 1 || n_p < 1 || ldo < n_s)
+        return fail(NQS_ERR_INVALID_ARG, "nqs_shard_sums: bad arguments");
+    CK(launch_shard_sums(jac_prec(precision), O, ldo, n_s, n_p, static_cast<const c128*>(eloc),
+                         static_cast<c128*>(osum_out), static_cast<c128*>(esum_out), static_cast<cudaStream_t>(stream)),
+       "shard sums");
+    return NQS_OK;
+}
+
+int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, double weight, const int64_t* block_off,
+                          int32_t n_blocks, const void* eloc, const void* Omean_in, const void* Emean_in,
+                          int32_t precision, void* S_packed, void* F_out, nqs_workspace* ws, void* stream) {
+    if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if (!O || !eloc || !Omean_in || !Emean_in || !S_packed || !F_out || n_s < 1 || n_p < 1 || ldo < n_s ||
+        !(weight > 0.0))
+        return fail(NQS_ERR_INVALID_ARG, "qgt_block_build_shard: bad arguments");
+    int rc = check_offsets(block_off, n_blocks, n_p);
+    if (rc) return rc;
+    Arena a = arena_of(ws);
+    BuildBufs bb;
+    plan_build(a, n_s, n_p, precision, &bb);
+    rc = check_ws(ws, a);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* status = status_of(ws);
+    const int nsp = nsplit_of(precision);
+    c128* S = static_cast<c128*>(S_packed);
+    CK(launch_ecenter(static_cast<const c128*>(eloc), n_s, static_cast<const c128*>(Emean_in), bb.e, st), "ecenter");
+    CK(launch_center(precision, nsp, O, ldo, n_s, n_p, nullptr, bb.e, static_cast<c128*>(F_out), nullptr,
+                     nsp ? bb.planes : nullptr, bb.ldk, bb.diag, bb.gexp, n_p, status, st,
+                     static_cast<const c128*>(Omean_in), weight),
+       "center");
+    GramTable* tab = new (std::nothrow) GramTable;
+    if (!tab) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    gram_table(block_off, n_blocks, 64, tab);
+    cudaError_t e;
+    if (nsp) {
+        e = launch_gram_tc(nsp, bb.planes, bb.gexp, n_p, 2 * n_p, bb.ldk, bb.ldk, weight, *tab, S, status, st);
+        if (e == cudaSuccess) e = launch_set_diag(S, *tab, bb.diag, st);
+    } else {
+        e = launch_gram_simt(precision, O, ldo, n_s, nullptr, weight, *tab, S, st);
+    }
+    delete tab;
+    if (e == cudaErrorNotSupported) return fail(NQS_ERR_UNSUPPORTED, "tensor-core Gram needs an sm_103 device");
+    CK(e, "gram");
+    return NQS_OK;
+}
+
 int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, const void* F, double diag_shift,
                     double cutoff, int32_t cutoff_mode, double eta, int32_t solver, void* dtheta_out,
                     double* evals_out, int32_t* n_kept_out, nqs_workspace* ws, void* stream) {

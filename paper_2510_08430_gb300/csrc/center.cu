@@ -12,6 +12,55 @@
 
 namespace nqs {
 
+// Inputs of one shard of a sample-sharded step: the global means (instead of the shard's
+// own) and the weight of every sample (1/N over all shards). Both unused when NULL/0.
+struct ShardArgs {
+    const c128* mean_in;
+    double wconst;
+};
+
+// e = E_loc - <E> with the global <E> of a sample-sharded step.
+__global__ void ecenter_kernel(const c128* __restrict__ eloc, long long ns, const c128* __restrict__ emean,
+                               c128* __restrict__ e) {
+    const c128 m = emean[0];
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x)
+        e[s] = eloc[s] - m;
+}
+
+// out[p] = sum_s X[p][s] (FP64), the per-shard sums behind the global means.
+template <typename R>
+__global__ void __launch_bounds__(256) rowsum_kernel(const cx<R>* __restrict__ X, long long ldx, long long ns,
+                                                      c128* __restrict__ out) {
+    __shared__ double sh[32];
+    const cx<R>* row = X + blockIdx.x * ldx;
+    double re = 0.0, im = 0.0;
+    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+        re += (double)row[s].re;
+        im += (double)row[s].im;
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = mk<double>(re, im);
+}
+
+cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long ns, long long np, const c128* eloc,
+                              c128* osum, c128* esum, cudaStream_t st) {
+    count_launch();
+    if (prec == NQS_FP32)
+        rowsum_kernel<float><<<(unsigned)np, 256, 0, st>>>((const c64*)O, ldo, ns, osum);
+    else
+        rowsum_kernel<double><<<(unsigned)np, 256, 0, st>>>((const c128*)O, ldo, ns, osum);
+    count_launch();
+    rowsum_kernel<double><<<1, 256, 0, st>>>(eloc, ns, ns, esum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st) {
+    count_launch();
+    ecenter_kernel<<<(unsigned)((ns + 255) / 256 < 1024 ? (ns + 255) / 256 : 1024), 256, 0, st>>>(eloc, ns, emean, e);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(1024) emean_kernel(const c128* __restrict__ eloc, const double* __restrict__ w,
                                                       long long ns, c128* __restrict__ emean,
                                                       c128* __restrict__ e, DevStatus* status) {
@@ -52,13 +101,14 @@ template <typename R>
 __global__ void __launch_bounds__(256) center_kernel(cx<R>* __restrict__ O, long long ldo, long long ns,
                                                       const double* __restrict__ w, const c128* __restrict__ e,
                                                       c128* __restrict__ F, c128* __restrict__ Omean,
-                                                      DevStatus* status) {
+                                                      ShardArgs sa, DevStatus* status) {
     __shared__ double sh[32];
     const long long p = blockIdx.x;
     cx<R>* row = O + p * ldo;
     const double u = 1.0 / (double)ns;
+    const double uw = sa.wconst > 0.0 ? sa.wconst : u;  // weight of every sample when w is NULL
     double mr = 0.0, mi = 0.0;
-    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+    for (long long s = threadIdx.x; s < (sa.mean_in ? 0 : ns); s += blockDim.x) {
         const cx<R> v = row[s];
         const double ws = w ? w[s] : 1.0;
         mr = fma(ws, (double)v.re, mr);
@@ -70,10 +120,14 @@ __global__ void __launch_bounds__(256) center_kernel(cx<R>* __restrict__ O, long
         mr *= u;
         mi *= u;
     }
+    if (sa.mean_in) {  // global mean of a sample-sharded step
+        mr = sa.mean_in[p].re;
+        mi = sa.mean_in[p].im;
+    }
     double fr = 0.0, fi = 0.0;
     for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
         const cx<R> v = row[s];
-        const double ws = w ? w[s] : u;
+        const double ws = w ? w[s] : uw;
         const cx<R> d = mk<R>((R)((double)v.re - mr), (R)((double)v.im - mi));
         row[s] = d;
         const c128 es = e[s];
@@ -99,13 +153,15 @@ __global__ void __launch_bounds__(256) center_split_kernel(const c128* __restric
                                                             c128* __restrict__ Omean, __nv_bfloat16* __restrict__ pl0,
                                                             __nv_bfloat16* __restrict__ pl1,
                                                             __nv_bfloat16* __restrict__ pl2, long long ldk,
-                                                            double* __restrict__ diag, DevStatus* status) {
+                                                            double* __restrict__ diag, ShardArgs sa,
+                                                            DevStatus* status) {
     __shared__ double sh[32];
     const long long p = blockIdx.x;
     const c128* row = O + p * ldo;
     const double u = 1.0 / (double)ns;
+    const double uw = sa.wconst > 0.0 ? sa.wconst : u;  // weight of every sample when w is NULL
     double mr = 0.0, mi = 0.0;
-    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+    for (long long s = threadIdx.x; s < (sa.mean_in ? 0 : ns); s += blockDim.x) {
         const c128 v = row[s];
         const double ws = w ? w[s] : 1.0;
         mr = fma(ws, v.re, mr);
@@ -117,13 +173,17 @@ __global__ void __launch_bounds__(256) center_split_kernel(const c128* __restric
         mr *= u;
         mi *= u;
     }
+    if (sa.mean_in) {  // global mean of a sample-sharded step
+        mr = sa.mean_in[p].re;
+        mi = sa.mean_in[p].im;
+    }
     double fr = 0.0, fi = 0.0, dg = 0.0;
     __nv_bfloat16* pls[3] = {pl0, pl1, pl2};
     for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
         double dr = 0.0, di = 0.0;
         if (s < ns) {
             const c128 v = row[s];
-            const double ws = w ? w[s] : u;
+            const double ws = w ? w[s] : uw;
             dr = v.re - mr;
             di = v.im - mi;
             const c128 es = e[s];
@@ -206,13 +266,14 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
                                                             __nv_bfloat16* __restrict__ pl3,
                                                             __nv_bfloat16* __restrict__ pl4, int8_t* __restrict__ gexp,
                                                             long long gstride, long long ldk, double* __restrict__ diag,
-                                                            DevStatus* status) {
+                                                            ShardArgs sa, DevStatus* status) {
     __shared__ double sh[32];
     const long long p = blockIdx.x;
     const c128* row = O + p * ldo;
     const double u = 1.0 / (double)ns;
+    const double uw = sa.wconst > 0.0 ? sa.wconst : u;  // weight of every sample when w is NULL
     double mr = 0.0, mi = 0.0;
-    for (long long s = threadIdx.x; s < ns; s += blockDim.x) {
+    for (long long s = threadIdx.x; s < (sa.mean_in ? 0 : ns); s += blockDim.x) {
         const c128 v = row[s];
         const double ws = w ? w[s] : 1.0;
         mr = fma(ws, v.re, mr);
@@ -224,6 +285,10 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         mr *= u;
         mi *= u;
     }
+    if (sa.mean_in) {  // global mean of a sample-sharded step
+        mr = sa.mean_in[p].re;
+        mi = sa.mean_in[p].im;
+    }
     double fr = 0.0, fi = 0.0, dg = 0.0;
     __nv_bfloat16* pls[5] = {pl0, pl1, pl2, pl3, pl4};
     // blockDim.x is a multiple of GROUP, so each group of 16 samples lies in one half-warp
@@ -231,7 +296,7 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         double dr = 0.0, di = 0.0;
         if (s < ns) {
             const c128 v = row[s];
-            const double ws = w ? w[s] : u;
+            const double ws = w ? w[s] : uw;
             dr = v.re - mr;
             di = v.im - mi;
             const c128 es = e[s];
@@ -302,7 +367,9 @@ cudaError_t launch_vjp(int prec, const void* O, long long ldo, long long ns, lon
 
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st) {
+                          double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st,
+                          const c128* mean_in, double wconst) {
+    const ShardArgs sa{mean_in, wconst};
     if (np <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)np;
     if (nsplit == 5) {
@@ -310,7 +377,7 @@ cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long lon
         center_group_kernel<<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean,
                                                   (__nv_bfloat16*)planes[0], (__nv_bfloat16*)planes[1],
                                                   (__nv_bfloat16*)planes[2], (__nv_bfloat16*)planes[3],
-                                                  (__nv_bfloat16*)planes[4], gexp, gstride, ldk, diag, status);
+                                                  (__nv_bfloat16*)planes[4], gexp, gstride, ldk, diag, sa, status);
     } else if (nsplit == 2 || nsplit == 3) {
         __nv_bfloat16* p0 = (__nv_bfloat16*)planes[0];
         __nv_bfloat16* p1 = (__nv_bfloat16*)planes[1];
@@ -318,16 +385,16 @@ cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long lon
         count_launch();
         if (nsplit == 2)
             center_split_kernel<2><<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk,
-                                                         diag, status);
+                                                         diag, sa, status);
         else
             center_split_kernel<3><<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean, p0, p1, p2, ldk,
-                                                         diag, status);
+                                                         diag, sa, status);
     } else if (prec == NQS_FP64) {
         count_launch();
-        center_kernel<double><<<grid, 256, 0, st>>>((c128*)O, ldo, ns, w, e, F, Omean, status);
+        center_kernel<double><<<grid, 256, 0, st>>>((c128*)O, ldo, ns, w, e, F, Omean, sa, status);
     } else {
         count_launch();
-        center_kernel<float><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, status);
+        center_kernel<float><<<grid, 256, 0, st>>>((c64*)O, ldo, ns, w, e, F, Omean, sa, status);
     }
     return cudaGetLastError();
 }

@@ -72,11 +72,15 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 // split planes of dO (O is c128, unchanged)
 // (split modes also write diag[k] = sum_s w_s |dO_k(s)|^2 in FP64; nsplit 5 = grouped
 // error-free split with int8 exponents gexp[group][param], groups of 16 samples)
+cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long ns, long long np, const c128* eloc,
+                              c128* osum, c128* esum, cudaStream_t st);
+cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st);
 cudaError_t launch_vjp(int prec, const void* O, long long ldo, long long ns, long long np, const c128* g, c128* out,
                        cudaStream_t st);
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
                           const double* w, const c128* e, c128* F, c128* Omean, void* const* planes, long long ldk,
-                          double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st);
+                          double* diag, int8_t* gexp, long long gstride, DevStatus* status, cudaStream_t st,
+                          const c128* mean_in = nullptr, double wconst = 0.0);
 
 // ---- Gram ----
 struct GBlk {                   // one QGT block of one instance
