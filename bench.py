@@ -258,6 +258,25 @@ def compare_steps(nq, torch, np, w, model, ham, theta, x, dth, solver) -> dict:
         "seconds": tf, "blocks": [int(w.block_off[-1])],
         "dtheta_rel_diff_vs_block": err(dfull, dth),
         "note": "full-QGT update: a different method; it is not expected to equal the block-layer update"}
+    # the sample-space (NTK) form of the full-QGT update (FP32 N_s x N_s Gram, mixed solver),
+    # timed from the FP64 Jacobian and local energies
+    try:
+        _, O64 = nq.nqs_jacobian(model, theta, x, "fp64")
+        el64 = nq.nqs_local_energy(model, theta, x, ham, "fp64")
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        dntk, _ = nq.ntk_solve(O64, w.n_samples, el64, w.diag_shift, w.cutoff, 1.0, "fp32")
+        e.record()
+        e.synchronize()
+        dntk = dntk.cpu().numpy()
+        del O64, el64
+        out["ntk_fp32gram_mixedsolve"] = {
+            "seconds": s.elapsed_time(e) / 1e3, "what": "centring, N_s x N_s Gram, solve, back-projection",
+            "dtheta_rel_diff_vs_full_qgt": err(dntk, dfull)}
+    except Exception as exc:
+        out["ntk_fp32gram_mixedsolve"] = {"unavailable": str(exc)[:200]}
     for prec in ("fp32", "split_bf16", "split_bf16x3"):
         if prec == w.precision:
             continue

@@ -223,6 +223,23 @@ NQS_API int qgt_block_build_static(void* O, int64_t ldo, int64_t n_s, int64_t n_
                            int32_t precision, void* S_packed, void* F_out, void* Omean_out,
                            void* Emean_out, void* stream);
 
+/* ntk_solve -- the sample-space (NTK) form of the full-QGT update, the comparator of the
+ * block-layer step (equal to the full-QGT solve by the push-through identity when no
+ * eigenvalue is cut):
+ *   dtheta = -eta X^H (X X^H + diag_shift I)^{-1} eps,  X = dO / sqrt(N_s), eps = e / sqrt(N_s),
+ * dO = O - <O>, e = E_loc - <E>, uniform weights.
+ *   O        : c128 parameter-major Jacobian (nqs_jacobian, NQS_FP64), leading dimension
+ *              ldo; OVERWRITTEN with dO.
+ *   eloc     : c128 [n_s].   dtheta_out: c128 [n_p].   Emean_out: c128 [1] or NULL.
+ *   precision: arithmetic of the N_s x N_s Gram (NQS_FP64, or NQS_FP32 with the mixed
+ *              solver); the eigen-solve of X X^H + diag_shift I uses the per-block solver
+ *              with the relative cutoff `cutoff`.
+ *   Workspace: ntk_solve_workspace_size (holds an N_s x N_s complex128 matrix). */
+NQS_API int ntk_solve_workspace_size(int64_t n_s, int64_t n_p, int32_t precision, size_t* bytes);
+NQS_API int ntk_solve(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const void* eloc, double diag_shift,
+              double cutoff, double eta, int32_t precision, void* dtheta_out, void* Emean_out,
+              nqs_workspace* ws, void* stream);
+
 /* ---- sample sharding ----
  * A step over N samples split into shards (one per rank, or several on one GPU) needs
  * two exchanges: the global means before centring, and the sum of the shards' S and F.

@@ -63,6 +63,8 @@ SIGNATURES = {
     "nqs_local_energy": (C.c_int, [MP, P, P, I64, HP, I32, P, P, P]),
     "nqs_connections": (C.c_int, [P, I64, HP, P, P, P, I64, C.POINTER(C.c_int64), P, P]),
     "nqs_vjp": (C.c_int, [P, I64, I64, I64, I32, P, P, P]),
+    "ntk_solve_workspace_size": (C.c_int, [I64, I64, I32, SZ]),
+    "ntk_solve": (C.c_int, [P, I64, I64, I64, P, D, D, D, I32, P, P, P, P]),
     "nqs_shard_sums": (C.c_int, [P, I64, I64, I64, I32, P, P, P, P]),
     "qgt_block_build_shard": (C.c_int, [P, I64, I64, I64, D, OFF, I32, P, P, P, I32, P, P, P, P]),
     "qgt_block_build": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P, P]),

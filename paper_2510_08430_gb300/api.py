@@ -378,6 +378,22 @@ def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float
     return list(torch.split(dth, sizes)), em, ev, nk
 
 
+def ntk_solve(O: torch.Tensor, n_s: int, eloc: torch.Tensor, diag_shift: float, cutoff: float = 1e-10,
+              eta: float = 1.0, precision="fp64"):
+    """Sample-space (NTK) form of the full-QGT update from a c128 Jacobian O [n_p, ldo]
+    (overwritten with dO). Returns (dtheta c128 [n_p], Emean c128 [1])."""
+    lib = _lib.load()
+    p = _prec(precision)
+    n_p = int(O.shape[0])
+    ws = Workspace(_size(lib.ntk_solve_workspace_size, n_s, n_p, p), device=O.device)
+    dth = torch.empty(n_p, dtype=torch.complex128, device=O.device)
+    em = torch.empty(1, dtype=torch.complex128, device=O.device)
+    check(lib.ntk_solve(_ptr(O), int(O.shape[1]), n_s, n_p, _ptr(eloc), float(diag_shift), float(cutoff), float(eta),
+                        p, _ptr(dth), _ptr(em), ws.h, _stream()))
+    ws.sync_status()
+    return dth, em
+
+
 def launch_count() -> int:
     """Kernels launched by libnqs_sr in this process."""
     return int(_lib.load().nqs_launch_count())

@@ -558,6 +558,71 @@ int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, double
     return NQS_OK;
 }
 
+static void plan_ntk(Arena& a, long long ns, long long np, int prec, c128** e, c128** F, void** Y, long long* ldy,
+                     c128** S, c128** rhs, c128** u) {
+    *e = static_cast<c128*>(a.take(16 * (size_t)ns));
+    *F = static_cast<c128*>(a.take(16 * (size_t)np));
+    *ldy = round_up(np, 32);
+    *Y = a.take(csize(prec) * (size_t)ns * (size_t)(*ldy));
+    *S = static_cast<c128*>(a.take(16 * (size_t)ns * (size_t)ns));
+    *rhs = static_cast<c128*>(a.take(16 * (size_t)ns));
+    *u = static_cast<c128*>(a.take(16 * (size_t)ns));
+}
+
+int ntk_solve_workspace_size(int64_t n_s, int64_t n_p, int32_t precision, size_t* bytes) {
+    if (!bytes || n_s < 1 || n_p < 1 || (precision != NQS_FP64 && precision != NQS_FP32))
+        return fail(NQS_ERR_INVALID_ARG, "ntk_solve_workspace_size: bad arguments");
+    Arena a = sizing_arena();
+    c128 *e, *F, *S, *rhs, *u;
+    void* Y;
+    long long ldy;
+    plan_ntk(a, n_s, n_p, precision, &e, &F, &Y, &ldy, &S, &rhs, &u);
+    const int64_t off[2] = {0, n_s};
+    a.take(solve_workspace_bytes(off, 1));
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+int ntk_solve(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const void* eloc, double diag_shift, double cutoff,
+              double eta, int32_t precision, void* dtheta_out, void* Emean_out, nqs_workspace* ws, void* stream) {
+    if (precision != NQS_FP64 && precision != NQS_FP32)
+        return fail(NQS_ERR_INVALID_ARG, "ntk_solve: precision must be NQS_FP64 or NQS_FP32");
+    if (!O || !eloc || !dtheta_out || n_s < 1 || n_p < 1 || ldo < n_s)
+        return fail(NQS_ERR_INVALID_ARG, "ntk_solve: bad arguments");
+    Arena a = arena_of(ws);
+    c128 *e, *F, *S, *rhs, *u;
+    void* Y;
+    long long ldy;
+    plan_ntk(a, n_s, n_p, precision, &e, &F, &Y, &ldy, &S, &rhs, &u);
+    const int64_t off[2] = {0, n_s};
+    Arena need = a;
+    need.take(solve_workspace_bytes(off, 1));
+    int rc = check_ws(ws, need);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* status = status_of(ws);
+    CK(launch_emean(static_cast<const c128*>(eloc), nullptr, n_s, static_cast<c128*>(Emean_out), e, status, st),
+       "emean");
+    CK(launch_center(NQS_FP64, 0, O, ldo, n_s, n_p, nullptr, e, F, nullptr, nullptr, 0, nullptr, nullptr, n_p, status,
+                     st),
+       "center");
+    CK(launch_ntk_transpose(precision, static_cast<const c128*>(O), ldo, n_s, n_p, Y, ldy, st), "transpose");
+    GramTable* tab = new (std::nothrow) GramTable;
+    if (!tab) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    gram_table(off, 1, 64, tab);
+    cudaError_t err = launch_gram_simt(precision, Y, ldy, ldy, nullptr, 1.0 / (double)n_s, *tab, S, st);
+    delete tab;
+    CK(err, "sample gram");
+    CK(launch_ntk_rhs(e, n_s, rhs, st), "rhs");
+    // u = (S_T + lambda I)^{-1} conj(eps): the block solver's dtheta with eta = -1
+    rc = run_solve(S, off, 1, rhs, diag_shift, cutoff, 0, -1.0,
+                   precision == NQS_FP64 ? NQS_SOLVE_FP64 : NQS_SOLVE_MIXED_PSD, u, nullptr, nullptr, a, status, st);
+    if (rc) return rc;
+    CK(launch_ntk_back(static_cast<const c128*>(O), ldo, n_s, n_p, u, eta, static_cast<c128*>(dtheta_out), st),
+       "back");
+    return NQS_OK;
+}
+
 int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_blocks, const void* F, double diag_shift,
                     double cutoff, int32_t cutoff_mode, double eta, int32_t solver, void* dtheta_out,
                     double* evals_out, int32_t* n_kept_out, nqs_workspace* ws, void* stream) {

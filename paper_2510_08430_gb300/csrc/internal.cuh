@@ -75,6 +75,12 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long ns, long long np, const c128* eloc,
                               c128* osum, c128* esum, cudaStream_t st);
 cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st);
+// sample-space (NTK) comparator
+cudaError_t launch_ntk_transpose(int prec, const c128* O, long long ldo, long long ns, long long np, void* Y,
+                                 long long ldy, cudaStream_t st);
+cudaError_t launch_ntk_rhs(const c128* e, long long ns, c128* rhs, cudaStream_t st);
+cudaError_t launch_ntk_back(const c128* O, long long ldo, long long ns, long long np, const c128* u, double eta,
+                            c128* dtheta, cudaStream_t st);
 cudaError_t launch_vjp(int prec, const void* O, long long ldo, long long ns, long long np, const c128* g, c128* out,
                        cudaStream_t st);
 cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long long ns, long long np,
