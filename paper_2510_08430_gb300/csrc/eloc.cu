@@ -261,6 +261,170 @@ __device__ __forceinline__ void df_mac(float& ah, float& al, float xh, float xl,
     al = __fadd_rn(al, __fadd_rn(e, pl));
 }
 
+// ---- ln cosh in double-float arithmetic (the hidden units of the connected forwards)
+// Building blocks: TwoSum/Fast-TwoSum (Knuth; Dekker 1971) and the FMA-based exact product.
+// exp: x = k ln2 + r (ln2 in three parts, the first with 8 trailing zero bits so that k ln2_1
+// is exact for |k| < 256), expm1(r 2^-10) by its Taylor series, then ten doublings
+// expm1(2y) = expm1(y)(2 + expm1(y)). sin/cos: h = k pi/2 + r (three-part pi/2), Taylor series
+// at r/8, three doublings sin 2a = 2 sin a cos a, cos 2a = 1 - 2 sin^2 a, quadrant from k.
+// log and atan2: one Newton step from the FP32 value. About 2^-46 relative; the rare
+// arguments outside the reductions' ranges take the FP64 ln cosh.
+namespace dfm {
+struct dff {
+    float h, l;
+};
+__device__ __forceinline__ dff mkf(float h, float l) {
+    dff r;
+    r.h = h;
+    r.l = l;
+    return r;
+}
+__device__ __forceinline__ dff fts(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return mkf(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dff add(dff a, dff b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return fts(s, e);
+}
+__device__ __forceinline__ dff mul(dff a, dff b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    return fts(p, e);
+}
+__device__ __forceinline__ dff prodf(float a, float b) {  // exact a b
+    const float p = __fmul_rn(a, b);
+    return mkf(p, fmaf(a, b, -p));
+}
+__device__ __forceinline__ dff neg(dff a) { return mkf(-a.h, -a.l); }
+__device__ __forceinline__ dff scl(dff a, float s) { return mkf(a.h * s, a.l * s); }  // s a power of two
+__device__ __forceinline__ dff from_double(double x) {
+    const float h = __double2float_rn(x);
+    return mkf(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }  // -126 <= k <= 127
+
+__device__ __forceinline__ dff expm1_core(dff r) {  // |r| <= ln2 / 2
+    const dff rs = scl(r, 0x1p-10f);
+    dff p = mkf(0x1.111112p-7f, -0x1.dddddep-32f);
+    p = add(mul(p, rs), mkf(0x1.555556p-5f, -0x1.555556p-30f));
+    p = add(mul(p, rs), mkf(0x1.555556p-3f, -0x1.555556p-28f));
+    p = add(mul(p, rs), mkf(0x1p-1f, 0.f));
+    p = add(mul(p, rs), mkf(1.f, 0.f));
+    dff e = mul(p, rs);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) e = mul(e, add(mkf(2.f, 0.f), e));
+    return e;
+}
+// reduction x = k ln2 + r (|k| < 256)
+__device__ __forceinline__ dff red_ln2(dff x, float k) {
+    dff t = mkf(__fsub_rn(x.h, __fmul_rn(k, 0x1.62e4p-1f)), 0.f);
+    t = add(t, mkf(x.l, 0.f));
+    t = add(t, neg(prodf(k, 0x1.7f7d1cp-20f)));
+    return add(t, mkf(-__fmul_rn(k, 0x1.ef357ap-45f), 0.f));
+}
+// exp(y) for |y| <= 87
+__device__ __forceinline__ dff exp_df(dff y) {
+    const float k = rintf(y.h * 1.44269504f);
+    const dff o = add(mkf(1.f, 0.f), expm1_core(red_ln2(y, k)));
+    return scl(o, pow2f((int)k));
+}
+// rho = exp(x) and om = 1 - rho for x <= 0
+__device__ __forceinline__ void exp_om(dff x, dff* rho, dff* om) {
+    if (x.h < -60.f) {
+        *rho = mkf(0.f, 0.f);
+        *om = mkf(1.f, 0.f);
+        return;
+    }
+    const float k = rintf(x.h * 1.44269504f);
+    const dff e = expm1_core(red_ln2(x, k));
+    *rho = scl(add(mkf(1.f, 0.f), e), pow2f((int)k));
+    *om = (k == 0.f) ? neg(e) : add(mkf(1.f, 0.f), neg(*rho));
+}
+// (sin h, cos h) for |h| < 256 pi/2
+__device__ __forceinline__ void sincos_df(dff h, dff* sn, dff* cs) {
+    const float k = rintf(h.h * 0.636619772f);
+    dff t = mkf(__fsub_rn(h.h, __fmul_rn(k, 0x1.922p+0f)), 0.f);
+    t = add(t, mkf(h.l, 0.f));
+    t = add(t, neg(prodf(k, -0x1.2aeef4p-18f)));
+    t = add(t, mkf(-__fmul_rn(k, -0x1.73dcb4p-43f), 0.f));
+    const dff rs = scl(t, 0.125f);
+    const dff x2 = mul(rs, rs);
+    dff p = mkf(0x1.71de3ap-19f, 0x1.55b1ccp-45f);
+    p = add(mul(p, x2), mkf(-0x1.a01a02p-13f, 0x1.7f97fap-39f));
+    p = add(mul(p, x2), mkf(0x1.111112p-7f, -0x1.dddddep-32f));
+    p = add(mul(p, x2), mkf(-0x1.555556p-3f, 0x1.555556p-28f));
+    p = add(mul(p, x2), mkf(1.f, 0.f));
+    dff s = mul(p, rs);
+    dff c = mkf(-0x1.27e4fcp-22f, 0x1.10ec14p-47f);
+    c = add(mul(c, x2), mkf(0x1.a01a02p-16f, -0x1.7f97fap-42f));
+    c = add(mul(c, x2), mkf(-0x1.6c16c2p-10f, 0x1.27d27ep-35f));
+    c = add(mul(c, x2), mkf(0x1.555556p-5f, -0x1.555556p-30f));
+    c = add(mul(c, x2), mkf(-0x1p-1f, 0.f));
+    c = add(mul(c, x2), mkf(1.f, 0.f));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const dff s2 = scl(mul(s, c), 2.f);
+        c = add(mkf(1.f, 0.f), scl(mul(s, s), -2.f));
+        s = s2;
+    }
+    switch (((int)k) & 3) {
+        case 0: *sn = s; *cs = c; break;
+        case 1: *sn = c; *cs = neg(s); break;
+        case 2: *sn = neg(s); *cs = neg(c); break;
+        default: *sn = neg(c); *cs = s; break;
+    }
+}
+__device__ __forceinline__ dff log_df(dff x) {  // x > 1e-30
+    const float y0 = logf(x.h);
+    return add(mkf(y0, 0.f), add(mul(x, exp_df(mkf(-y0, 0.f))), mkf(-1.f, 0.f)));
+}
+__device__ __forceinline__ dff atan2_df(dff Y, dff X) {  // X >= 0
+    const float th = atan2f(Y.h, X.h);
+    dff s, c;
+    sincos_df(mkf(th, 0.f), &s, &c);
+    const dff num = add(mul(Y, c), neg(mul(X, s)));
+    const float den = fmaf(X.h, c.h, Y.h * s.h);
+    return den != 0.f ? add(mkf(th, 0.f), mkf(num.h / den, 0.f)) : mkf(th, 0.f);
+}
+// ln cosh(zr + i zi), same branch as clncosh; false when the argument is outside the
+// ranges above (the caller then takes the FP64 ln cosh).
+__device__ __forceinline__ bool lncosh_df(dff zr, dff zi, dff* re, dff* im) {
+    if (!(fabsf(zi.h) < 400.f)) return false;
+    const float s = zr.h >= 0.f ? 1.f : -1.f;
+    const dff ax = scl(zr, s), h = scl(zi, -s);
+    dff sh, ch, rho, om;
+    sincos_df(h, &sh, &ch);
+    exp_om(scl(ax, -2.f), &rho, &om);
+    const dff rc2 = mul(rho, mul(ch, ch));
+    const dff mod2 = add(mul(om, om), scl(rc2, 4.f));
+    if (!(mod2.h > 1e-30f)) return false;
+    const dff lr = scl(log_df(mod2), 0.5f);
+    const dff li = atan2_df(mul(rho, scl(mul(sh, ch), 2.f)), add(om, scl(rc2, 2.f)));
+    *re = add(add(ax, mkf(-0x1.62e43p-1f, 0x1.05c61p-29f)), lr);
+    *im = add(scl(zi, s), li);
+    return true;
+}
+}  // namespace dfm
+
+// ln cosh of a double-float complex value into the shared-memory layout
+__device__ __forceinline__ df2 lncosh_to_df2(dfm::dff zr, dfm::dff zi) {
+    dfm::dff re, im;
+    if (dfm::lncosh_df(zr, zi, &re, &im)) {
+        df2 d;
+        d.rh = re.h;
+        d.rl = re.l;
+        d.ih = im.h;
+        d.il = im.l;
+        return d;
+    }
+    return to_df(clncosh(mk<double>((double)zr.h + (double)zr.l, (double)zi.h + (double)zi.l)));
+}
+
 __global__ void split_weights_kernel(const c128* __restrict__ w, long long n, float4* __restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const df2 d = to_df(w[i]);
@@ -325,9 +489,9 @@ __global__ void __launch_bounds__(256) conn_terms_df_kernel(ModelDesc md, const 
             const c128 wi = W0T[(long long)si[r] * out0 + u];
             const c128 wj = W0T[(long long)sj[r] * out0 + u];
             const double ai = -2.0 * sxi[r], aj = -2.0 * sxj[r];
-            v = clncosh(mk<double>(z.re + ai * wi.re + aj * wj.re, z.im + ai * wi.im + aj * wj.im));
+            v = mk<double>(z.re + ai * wi.re + aj * wj.re, z.im + ai * wi.im + aj * wj.im);
         }
-        A[r * ld + u] = to_df(v);
+        A[r * ld + u] = r < rows ? lncosh_to_df2(dfm::from_double(v.re), dfm::from_double(v.im)) : to_df(v);
     }
     __syncthreads();
     for (int l = 1; l < md.L; ++l) {
@@ -356,11 +520,14 @@ __global__ void __launch_bounds__(256) conn_terms_df_kernel(ModelDesc md, const 
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int r = 4 * rg + q;
-                const c128 z = mk<double>((double)acc[q].rh + (double)acc[q].rl, (double)acc[q].ih + (double)acc[q].il);
                 if (last) {
-                    if (r < rows) lpn[r] = z;
+                    if (r < rows)
+                        lpn[r] = mk<double>((double)acc[q].rh + (double)acc[q].rl,
+                                            (double)acc[q].ih + (double)acc[q].il);
                 } else {
-                    B[r * ld + j] = to_df(clncosh(z));
+                    // renormalise the accumulated pair before ln cosh
+                    const dfm::dff zr = dfm::fts(acc[q].rh, acc[q].rl), zi = dfm::fts(acc[q].ih, acc[q].il);
+                    B[r * ld + j] = lncosh_to_df2(zr, zi);
                 }
             }
         }
