@@ -108,6 +108,7 @@ def trd_traffic(w, solver: str):
     when the summary is missing, is for another workload/solver, or the kernel source has
     changed since it was taken (sha256 of eigh_persist.cu recorded in the summary)."""
     import hashlib
+    import numpy as np
     path = os.path.join(ROOT, "profiles", f"trd_persist_{w.name}.md")
     src = os.path.join(ROOT, "paper_2510_08430_gb300", "csrc", "eigh_persist.cu")
     if not os.path.exists(path) or not os.path.exists(src):
@@ -118,8 +119,9 @@ def trd_traffic(w, solver: str):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             rec[k.strip()] = v.strip().strip("`")
-    if rec.get("source_sha256") != sha or rec.get("solver") != solver or rec.get("n_s") != str(w.n_samples):
-        return None
+    blocks = ",".join(str(int(v)) for v in np.diff(w.block_off))
+    if rec.get("source_sha256") != sha or rec.get("solver") != solver or rec.get("blocks") != blocks:
+        return None  # the reduction's traffic depends on the blocks only, not on N_s
     try:
         return float(rec["dram_bytes_per_launch"])
     except (KeyError, ValueError):
