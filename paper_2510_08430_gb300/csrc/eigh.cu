@@ -466,6 +466,64 @@ __global__ void to_fp32_kernel(const c128* __restrict__ S, long long n, c64* __r
         Sf[i] = ccast<float>(S[i]);
 }
 
+// Sturm count in FP32 on (d + shift, e^2) stored as floats: the number of eigenvalues of
+// T + shift I below x. The LDL^T pivot recurrence is backward stable, so the count is exact for
+// a tridiagonal within a few FP32 ulps of the stored one.
+__device__ __forceinline__ int sturm_count_f(const float* __restrict__ ds, const float* __restrict__ e2, int n,
+                                             float x, float pivmin) {
+    int cnt = 0;
+    float q = ds[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f;
+    for (int k = 1; k < n; ++k) {
+        q = (ds[k] - x) - __fdividef(e2[k - 1], q);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.f;
+    }
+    return cnt;
+}
+
+// multisect2 with FP32 Sturm counts (brackets kept in FP64)
+__device__ void multisect2_f(const float* ds, const float* e2, int n, int k0, int k1, double lo0, double hi0,
+                             float pivmin, double tol, double* out0, double* out1) {
+    __shared__ double blo[2], bhi[2];
+    __shared__ int cnt[1024];
+    const int half = blockDim.x / 2;
+    const int g = threadIdx.x / half, t = threadIdx.x % half;
+    const int k = g ? k1 : k0;
+    if (threadIdx.x == 0) {
+        blo[0] = blo[1] = lo0;
+        bhi[0] = bhi[1] = hi0;
+    }
+    __syncthreads();
+    for (int round = 0; round < 12; ++round) {
+        const bool open0 = !(bhi[0] - blo[0] <= tol), open1 = !(bhi[1] - blo[1] <= tol);
+        if (!open0 && !open1) break;
+        const double lo = blo[g], hi = bhi[g];
+        const double x = lo + (hi - lo) * (double)(t + 1) / (double)(half + 1);
+        cnt[threadIdx.x] = sturm_count_f(ds, e2, n, (float)x, pivmin);
+        __syncthreads();
+        if (t == 0) {
+            double nlo = lo, nhi = hi;
+            for (int s2 = 0; s2 < half; ++s2) {
+                const double xs = lo + (hi - lo) * (double)(s2 + 1) / (double)(half + 1);
+                if (cnt[g * half + s2] <= k) {
+                    nlo = xs;
+                } else {
+                    nhi = xs;
+                    break;
+                }
+            }
+            blo[g] = nlo;
+            bhi[g] = nhi;
+        }
+        __syncthreads();
+    }
+    *out0 = 0.5 * (blo[0] + bhi[0]);
+    *out1 = 0.5 * (blo[1] + bhi[1]);
+    __syncthreads();
+}
+
 // One CTA per block: FP32-based bounds; a block needs the FP64 path when an eigenvalue
 // might fall on the dropped side of the cutoff within the FP32 error. The bounds need
 // only ~1e-10 relative accuracy (the certificate allows 4e-5).
@@ -479,8 +537,18 @@ __global__ void __launch_bounds__(256) mix_cert_kernel(SolveBufs B, MixBufs M, i
     double lo, hi, emax;
     gersh_cta(d, e, e2, n, a.shift, &lo, &hi, &emax);
     const double pivmin = 1e-290 * fmax(1.0, emax);
+    float* ds = M.ds32 + blk.off;
+    float* ef = M.e232 + blk.off;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        ds[k] = (float)(d[k] + a.shift);
+        ef[k] = k + 1 < n ? (float)e2[k] : 0.f;
+    }
+    __syncthreads();
+    // the certificate allows 4e-5 sigma_max: FP32 counts to ~1e-6 of the Gershgorin span suffice
+    const float pivf = fmaxf(1e-30f, 1e-30f * (float)emax);
     double smax, smin;
-    multisect2(d, e2, n, a.shift, n - 1, 0, lo, hi, pivmin, 1e-10 * fmax(fabs(lo), fabs(hi)), &smax, &smin);
+    multisect2_f(ds, ef, n, n - 1, 0, lo, hi, pivf, 1e-6 * fmax(fabs(lo), fabs(hi)), &smax, &smin);
+    (void)pivmin;
     if (threadIdx.x != 0) return;
     const double err = 4e-5 * fabs(smax);  // bound on the FP32 reduction's eigenvalue error
     const double thr_hi = a.cutoff_mode == 0 ? a.cutoff * (smax + err) : a.cutoff;
@@ -611,7 +679,7 @@ static void build_table(const int64_t* block_off, int nb, Built* bt) {
 
 struct SolveLayoutAll {
     SolveLayout L;
-    size_t sf, tf, toff, pdot, bar, piv, lmul, mx, mr, r32, y32, w32, hp, rn, fn, done, fb, total;
+    size_t sf, tf, toff, pdot, bar, piv, lmul, ds32, e232, mx, mr, r32, y32, w32, hp, rn, fn, done, fb, total;
 };
 
 static SolveLayoutAll layout_all(const int64_t* off, int nb) {
@@ -635,6 +703,8 @@ static SolveLayoutAll layout_all(const int64_t* off, int nb) {
     A.pdot = take(8ull * 2 * totch * QNB);
     A.bar = take(64);
     A.piv = take(8ull * np);
+    A.ds32 = take(4ull * np);
+    A.e232 = take(4ull * np);
     A.lmul = take(8ull * np);
     A.mx = take(16ull * np);
     A.mr = take(16ull * np);
@@ -765,6 +835,8 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     M.d = B.d;
     M.e = B.e;
     M.piv = reinterpret_cast<double*>(W + LA.piv);
+    M.ds32 = reinterpret_cast<float*>(W + LA.ds32);
+    M.e232 = reinterpret_cast<float*>(W + LA.e232);
     M.lmul = reinterpret_cast<double*>(W + LA.lmul);
     M.x = reinterpret_cast<c128*>(W + LA.mx);
     M.r = reinterpret_cast<c128*>(W + LA.mr);

@@ -75,6 +75,7 @@ struct MixBufs {
     c64* pdot;            // panel dot products V_p^H y: [2][sum of row chunks][QNB]
     double *d, *e;        // FP32-reduced tridiagonal (stored in FP64)
     double *piv, *lmul;   // LDL^T of T + lambda I
+    float *ds32, *e232;   // FP32 d + lambda and e^2 for the certificate's Sturm counts
     c128 *x, *r;          // refinement iterate and residual (FP64)
     c64 *r32, *y32, *w32; // FP32 work vectors
     c128* hpart;          // FP64 Hermitian matvec partials (T^2 x 64 per block)
