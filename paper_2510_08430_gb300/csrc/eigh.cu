@@ -23,7 +23,7 @@ namespace nqs {
 
 
 struct SolveLayout {
-    size_t tab, d, e, e2, tau, f, v0, v1, w, x, z, ev, hp, info, bcol, pvf, pxv, ypart, zmat, total;
+    size_t tab, d, e, e2, tau, f, v0, v1, w, x, z, ev, info, bcol, pvf, pxv, ypart, zmat, total;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -52,7 +52,6 @@ static SolveLayout solve_layout(const int64_t* off, int nb) {
     L.x = take(16 * np);
     L.z = take(16 * np);
     L.ev = take(8 * np);
-    L.hp = take(sizeof(HouseP) * nb);
     L.info = take(sizeof(BlkInfo) * nb);
     L.bcol = take(16 * np);
     L.pvf = take(16ull * nb * MAXCH);
@@ -379,16 +378,12 @@ __global__ void __launch_bounds__(512) ql_solve_kernel(SolveBufs B, int nb, Solv
         __syncthreads();
     }
     // keep decision on the QL eigenvalues
-    __shared__ double s_max;
-    __shared__ int s_kept;
     if (threadIdx.x == 0) {
         double mx = -1e300;
         for (int k = 0; k < n; ++k) mx = fmax(mx, dd[k]);
-        s_max = mx;
         const double thr = a.cutoff_mode == 0 ? a.cutoff * mx : a.cutoff;
         int kept = 0;
         for (int k = 0; k < n; ++k) kept += dd[k] > thr;
-        s_kept = kept;
         B.info[blockIdx.x].n_kept = kept;
         B.info[blockIdx.x].sigma_max = mx;
         B.info[blockIdx.x].thr = thr;
@@ -679,7 +674,7 @@ static void build_table(const int64_t* block_off, int nb, Built* bt) {
 
 struct SolveLayoutAll {
     SolveLayout L;
-    size_t sf, tf, toff, pdot, bar, piv, lmul, ds32, e232, mx, mr, r32, y32, w32, hp, rn, fn, done, fb, total;
+    size_t sf, tf, toff, pdot, bar, piv, lmul, ds32, e232, mx, mr, r32, y32, w32, hpart, rn, fn, done, fb, total;
 };
 
 static SolveLayoutAll layout_all(const int64_t* off, int nb) {
@@ -711,7 +706,7 @@ static SolveLayoutAll layout_all(const int64_t* off, int nb) {
     A.r32 = take(8ull * np);
     A.y32 = take(8ull * np);
     A.w32 = take(8ull * np);
-    A.hp = take(16ull * ytot);
+    A.hpart = take(16ull * ytot);
     A.rn = take(8ull * nb * MAXDCH);
     A.fn = take(8ull * nb);
     A.done = take(4ull * nb);
@@ -754,7 +749,6 @@ static int solve_fp64(SolveBufs& B, const EBTab& tab, int nmax, const c128* F, c
     T.tau = B.tau;
     T.pvf = B.pvf;
     T.pxv = B.pxv;
-    T.hp = B.hp;
     if (a.ev_trd_start) cudaEventRecord(a.ev_trd_start, st);
     int rc = launch_trd_persist<double>(T, tab, B.bar, status, st);
     if (rc) return rc;
@@ -810,7 +804,6 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     B.w = reinterpret_cast<c128*>(W + L.w);
     B.x = reinterpret_cast<c128*>(W + L.x);
     B.z = reinterpret_cast<c128*>(W + L.z);
-    B.hp = reinterpret_cast<HouseP*>(W + L.hp);
     B.info = reinterpret_cast<BlkInfo*>(W + L.info);
     B.bcol = reinterpret_cast<c128*>(W + L.bcol);
     B.pvf = reinterpret_cast<c128*>(W + L.pvf);
@@ -843,7 +836,7 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     M.r32 = reinterpret_cast<c64*>(W + LA.r32);
     M.y32 = reinterpret_cast<c64*>(W + LA.y32);
     M.w32 = reinterpret_cast<c64*>(W + LA.w32);
-    M.hpart = reinterpret_cast<c128*>(W + LA.hp);
+    M.hpart = reinterpret_cast<c128*>(W + LA.hpart);
     M.rn = reinterpret_cast<double*>(W + LA.rn);
     M.fn = reinterpret_cast<double*>(W + LA.fn);
     M.done = reinterpret_cast<int*>(W + LA.done);
@@ -868,7 +861,6 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     T.tau = B.tau;
     T.pvf = B.pvf;
     T.pxv = B.pxv;
-    T.hp = B.hp;
     if (a.ev_trd_start) cudaEventRecord(a.ev_trd_start, st);
     int rc = launch_trd_persist<float>(T, tab, B.bar, status, st);
     if (rc) return rc;

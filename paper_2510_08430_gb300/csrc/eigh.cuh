@@ -25,10 +25,6 @@ struct EBTab {
     int nb;
     EBlk b[MAXB];
 };
-struct HouseP {       // per-block scalars of the current reflector
-    c128 scale;       // 1 / (alpha - beta)
-    c128 tau;
-};
 struct BlkInfo {
     double sigma_max;
     double thr;
@@ -42,7 +38,6 @@ struct SolveBufs {
     c128* S;
     double *d, *e, *e2, *ev;
     c128 *tau, *f, *v0, *v1, *w, *x, *z;
-    HouseP* hp;
     BlkInfo* info;
     c128* bcol;          // column buffer of the reduction (c64 view in the FP32 reduction)           // column-norm partials of the reduction [nb][MAXDCH][2]
     c128 *pvf, *pxv, *ypart;
@@ -59,7 +54,6 @@ template <typename R> struct TrdBufs {
     double *d, *e, *e2;
     c128 *tau, *pvf, *pxv;
     cx<R>* bcol;          // next column, updated except for the alpha part of the last reflector
-    HouseP* hp;
 };
 
 constexpr int QNB = 32;      // reflectors per panel of the blocked (WY) application of Q

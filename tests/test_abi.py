@@ -78,3 +78,24 @@ def test_invalid_arguments_are_rejected(lib):
     off = (C.c_int64 * 3)(0, 100, 2368)
     assert lib.qgt_block_build_workspace_size(16, 999, off, 2, 0, C.byref(out)) == -1  # n_p mismatch
     assert lib.nqs_workspace_create(None, 1024, C.byref(C.c_void_p())) == -1
+
+
+def test_newer_entry_points_validate_on_the_host(lib):
+    """Argument errors of the batched, sharded, NTK and VJP calls are caught before any
+    device work (the fake pointers below are never dereferenced)."""
+    from paper_2510_08430_gb300 import _lib
+    out = C.c_size_t(0)
+    fake = C.c_void_p(256)
+    # batched: no instance
+    assert lib.sr_step_batched_workspace_size(0, None, None, None, None, None, 0, C.byref(out)) == -1
+    # NTK: split precisions are not an NTK Gram option
+    assert lib.ntk_solve_workspace_size(64, 100, _lib.NQS_SPLIT_BF16_EXACT, C.byref(out)) == -1
+    assert lib.ntk_solve_workspace_size(64, 100, _lib.NQS_FP32, C.byref(out)) == 0 and out.value > 64 * 64 * 16
+    # shard build: weight must be positive
+    off = (C.c_int64 * 2)(0, 10)
+    assert lib.qgt_block_build_shard(fake, 64, 64, 10, 0.0, off, 1, fake, fake, fake, 0, fake, fake, None,
+                                     None) == -1
+    assert b"qgt_block_build_shard" in lib.nqs_last_error()
+    # shard sums and VJP: leading dimension below n_s
+    assert lib.nqs_shard_sums(fake, 10, 64, 10, 0, fake, fake, fake, None) == -1
+    assert lib.nqs_vjp(fake, 10, 64, 10, 0, fake, fake, None) == -1
