@@ -309,7 +309,8 @@ def run_reference(args, rank: int, world: int) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_desc(w, "fp64"),
+        "config": workload_desc(w, "mixed"),
+        "reference_impl": "FP64 NumPy oracle (same workload and metric; FP64 Jacobian, E_loc, Gram and LAPACK eigh)",
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": info["cores"], "kind": "oracle",
                          "sample": info["sample"]},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
