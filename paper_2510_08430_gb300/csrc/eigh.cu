@@ -576,6 +576,18 @@ __global__ void retry_status_kernel(const int* __restrict__ fallback, int nb, De
     if (__any_sync(0xffffffffu, any) && threadIdx.x == 0) set_status(status, NQS_ERR_RETRY, W_SOLVE, -1);
 }
 
+// (h, l) += a b for FP32 a, b: exact product by FMA, TwoSum into the high word, errors to
+// the low word (double-float accumulation).
+__device__ __forceinline__ void df_acc(float& h, float& l, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    const float s = __fadd_rn(h, p);
+    const float bb = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, pe));
+}
+
 // T factor of each panel (forward, columnwise): T[j][j] = tau_j,
 // T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^H v_j), V = reflectors i0 .. i0+nbp-1.
 __global__ void __launch_bounds__(256) qt_factor_kernel(SolveBufs B, MixBufs M) {
@@ -588,16 +600,28 @@ __global__ void __launch_bounds__(256) qt_factor_kernel(SolveBufs B, MixBufs M) 
     if (i0 >= n - 1) return;
     const int nbp = (n - 1 - i0) < QNB ? (n - 1 - i0) : QNB;
     const c64* A = M.Sf + blk.soff;
-    // G = V^H V over rows r in [i0+1, n); V[r][j] = A[(i0+j) n + r] for r >= i0+j+1, else 0
-    for (int idx = threadIdx.x; idx < nbp * nbp; idx += blockDim.x) {
-        const int a = idx / nbp, b = idx % nbp;
-        if (b < a) continue;
-        c128 acc = mk<double>(0.0, 0.0);
+    // G = V^H V over rows r in [i0+1, n); V[r][j] = A[(i0+j) n + r] for r >= i0+j+1, else 0.
+    // The products of the FP32 reflector entries are made exact with an FMA and summed in
+    // double-float (hi + lo) on the FP32 units, about 2^-46 relative.
+    const int npairs = nbp * (nbp + 1) / 2;
+    for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+        int b = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);  // pair (a, b), a <= b
+        while ((b + 1) * (b + 2) / 2 <= idx) ++b;
+        while (b * (b + 1) / 2 > idx) --b;
+        const int a = idx - b * (b + 1) / 2;
         const int r0 = i0 + b + 1;  // both vectors nonzero from max(a, b) + i0 + 1
         const c64* va = A + (long long)(i0 + a) * n;
         const c64* vb = A + (long long)(i0 + b) * n;
-        for (int r = r0; r < n; ++r) cmacc(acc, ccast<double>(va[r]), ccast<double>(vb[r]));
-        G[a][b] = acc;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll 4
+        for (int r = r0; r < n; ++r) {
+            const c64 x = va[r], y = vb[r];  // conj(x) y
+            df_acc(rh, rl, x.re, y.re);
+            df_acc(rh, rl, x.im, y.im);
+            df_acc(ih, il, x.re, y.im);
+            df_acc(ih, il, -x.im, y.re);
+        }
+        G[a][b] = mk<double>((double)rh + (double)rl, (double)ih + (double)il);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
