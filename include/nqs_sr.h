@@ -57,7 +57,9 @@ extern "C" {
                                       retake it without NQS_GRAPH (the FP64 path then runs) */
 
 /* ---- precision of the sample-space contractions (Jacobian, E_loc, Gram) ----
- * NQS_FP64        : everything in FP64; O is c128.
+ * NQS_FP64        : everything in FP64 (O is c128), except that the local energies' FFNN
+ *                   hidden layers (products and ln cosh of the connected forwards) use
+ *                   double-float arithmetic (pairs of FP32 numbers, about 2^-46 relative).
  * NQS_FP32        : Jacobian and E_loc in FP32 (O is c64), centring and force
  *                   accumulated in FP64, Gram in FP32 FFMA.
  * NQS_SPLIT_BF16  : Jacobian and E_loc in FP64 (O is c128), and the Gram on
@@ -75,7 +77,8 @@ extern "C" {
  *                   fifteen products (every term above 2^-32 of the group scale) per group,
  *                   groups summed in double-float. Better than FP32 rounding of the data
  *                   even on heavy-tailed Jacobian rows.
- * The per-block shifted eigen-decomposition and solve is FP64 in every mode. */
+ * Local energies in the split modes are those of NQS_FP64. The per-block shifted
+ * eigen-decomposition and solve is selected separately (solver argument, below). */
 typedef enum {
     NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3, NQS_SPLIT_BF16_EXACT = 4
 } nqs_precision;
@@ -165,7 +168,8 @@ NQS_API int nqs_vjp(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_
 /* nqs_local_energy -- E_loc(x_s) (Eq. 1) for the Hamiltonian h:
  *   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign_rule psi(x^{ij})/psi(x) ],
  * x^{ij} = x with spins i and j flipped; connected configurations are visited in
- * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32, else FP64. */
+ * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32; otherwise FP64, with the
+ * FFNN hidden layers of the connected forwards in double-float (about 2^-46 relative). */
 NQS_API int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
                      const nqs_hamiltonian* h, int32_t precision, void* eloc_out,
                      nqs_workspace* ws, void* stream);
