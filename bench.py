@@ -172,7 +172,7 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle (bounded sample)
-def oracle_sample(w, n_sample: int = 256, eig_n: int = 1024) -> dict:
+def oracle_sample(w, n_sample: int = 1024, eig_n: int = 2048) -> dict:
     """Time the FP64 oracle on a bounded sample of the workload and extrapolate one step.
 
     Stages linear in N_s (Jacobian, E_loc, centring, force, block Gram) run on
