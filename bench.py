@@ -56,8 +56,8 @@ SOLVER_DESC = {"fp64": "FP64 Householder eigensolver",
 def workload_desc(w, solver="mixed") -> dict:
     import numpy as np
     return {
-        "workload": f"{w.name}: widths {list(w.model.widths)}, {w.bond_ij.shape[0]} bonds, "
-                    f"N_s={w.n_samples}, blocks {list(np.diff(w.block_off))}, {w.precision} Gram, "
+        "workload": f"{w.name}: widths {[int(v) for v in w.model.widths]}, {int(w.bond_ij.shape[0])} bonds, "
+                    f"N_s={int(w.n_samples)}, blocks {[int(v) for v in np.diff(w.block_off)]}, {w.precision} Gram, "
                     f"{SOLVER_DESC[solver]}",
         "solver": solver,
         "n_s": int(w.n_samples),

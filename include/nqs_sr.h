@@ -67,7 +67,9 @@ extern "C" {
  *                   (BF16 roundings of x and of the remainder) and three products
  *                   (hi*hi, hi*lo, lo*hi) are accumulated in FP32 over one
  *                   64-sample block at a time; the blocks are summed in
- *                   double-float. Entry representation error 2^-17.
+ *                   double-float. Entry representation error 2^-17. A reduced-accuracy
+ *                   mode: its dtheta bar is 1e-2 relative (it misses the 1e-6 bar of the
+ *                   split path on the 10x10 lattice; NQS_SPLIT_BF16_EXACT meets it).
  * NQS_SPLIT_BF16X3: as NQS_SPLIT_BF16 with hi + mid + lo and six products
  *                   (all terms above 2^-16 relative): representation error 2^-25.
  * NQS_SPLIT_BF16_EXACT: error-free split on the tensor cores: for every parameter and
@@ -212,9 +214,11 @@ NQS_API int qgt_block_build(void* O, int64_t ldo, int64_t n_s, int64_t n_p, cons
  *                any other value returns NQS_ERR_INVALID_ARG.
  *   n_s        : at most NQS_STATIC_MAX_SAMPLES; larger n_s returns
  *                NQS_ERR_INVALID_ARG before anything is launched.
- * Set-up: the first call on each device (with that device current) looks up the
- * device address of the static array once and caches it; make that first call
- * outside any stream capture.
+ * Set-up: every call whose stream is not capturing looks up the device address of the
+ * static array on the current device (cudaGetSymbolAddress) and caches it per device; a
+ * call during stream capture uses the cached address. So the first call on each device
+ * (with that device current) must be made outside any stream capture, and a device reset
+ * is picked up by the next uncaptured call. All pointers must belong to the current device.
  * Nothing in the static array has to start at zero: every element is written by the
  * call before it is read.
  * There is no device-side status: a non-finite O or E_loc shows as NaN/Inf in the
@@ -250,19 +254,24 @@ NQS_API int ntk_solve(void* O, int64_t ldo, int64_t n_s, int64_t n_p, const void
  * nqs_shard_sums -- osum_out[k] = sum_{s in shard} O[k*ldo + s] (c128 [n_p]) and
  *   esum_out[0] = sum_{s in shard} E_loc(s) (c128 [1]); FP64 accumulation. Summed over
  *   all shards and divided by N they give <O> and <E>. No workspace.
- * qgt_block_build_shard -- a shard's part of qgt_block_build: with the GLOBAL means
- *   Omean_in (c128 [n_p]) and Emean_in (c128 [1]) and weight = 1/N for every sample,
- *     S_packed = weight sum_{s in shard} dO_s^H dO_s (lower triangles, as qgt_block_build),
- *     F_out    = weight sum_{s in shard} conj(dO_s) e_s,
+ * qgt_block_build_shard -- a shard's part of qgt_block_build. Osum_in (c128 [n_p]) and
+ *   Esum_in (c128 [1]) are the sums of nqs_shard_sums over ALL shards (the all-reduced
+ *   sums), n_total the number of samples over all shards. The library forms the global means
+ *   <O> = Osum_in / n_total, <E> = Esum_in / n_total (copied to Omean_out, c128 [n_p], and
+ *   Emean_out, c128 [1], when not NULL) and, with weight 1/n_total for every sample,
+ *     S_packed = sum_{s in shard} dO_s^H dO_s / n_total (lower triangles, as qgt_block_build),
+ *     F_out    = sum_{s in shard} conj(dO_s) e_s / n_total,
  *   dO = O - <O>, e = E_loc - <E>. The sums over all shards of S_packed and F_out are
  *   qgt_block_build's S and F of all N samples. O is overwritten with dO in the
- *   FP64/FP32 modes (as qgt_block_build). Workspace: qgt_block_build_workspace_size. */
+ *   FP64/FP32 modes (as qgt_block_build). n_total < n_s is NQS_ERR_INVALID_ARG.
+ *   Workspace: qgt_block_build_workspace_size. */
 NQS_API int nqs_shard_sums(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t precision,
                    const void* eloc, void* osum_out, void* esum_out, void* stream);
-NQS_API int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, double weight,
+NQS_API int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, int64_t n_total,
                           const int64_t* block_off, int32_t n_blocks, const void* eloc,
-                          const void* Omean_in, const void* Emean_in, int32_t precision,
-                          void* S_packed, void* F_out, nqs_workspace* ws, void* stream);
+                          const void* Osum_in, const void* Esum_in, int32_t precision,
+                          void* S_packed, void* F_out, void* Omean_out, void* Emean_out,
+                          nqs_workspace* ws, void* stream);
 
 /* ---- per-block solver ----
  * NQS_SOLVE_FP64 : the Householder reduction, eigenvalues and solve all in FP64.
@@ -354,6 +363,15 @@ NQS_API int sr_step_batched(int32_t n_inst, const nqs_model* models, const void*
  * returns the milliseconds of each stage of the most recent timed sr_step.
  * nqs_launch_count returns the number of kernels this library has launched in
  * the process (all threads). */
+/* nqs_set_limits -- test hook of the failure paths (process-wide, all devices; takes effect
+ * for calls made after it returns). max_sweeps > 0 replaces both the implicit-QL sweep limit
+ * per eigenvalue (default 60) and the iterative-refinement sweep limit (default 30); a limit
+ * that runs out records NQS_ERR_NOT_CONVERGED. wait_ns > 0 replaces the budget of every
+ * device-side wait of the persistent solver kernels (grid barriers, wavefront flags; default
+ * 2 s); a wait that runs out records NQS_ERR_TIMEOUT and its kernel returns. 0 restores a
+ * default. Results computed under lowered limits are not the definition's. */
+NQS_API int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns);
+
 NQS_API int nqs_stage_timing(nqs_workspace* ws, int32_t enable);
 NQS_API int nqs_stage_times(nqs_workspace* ws, double* ms_out, int32_t max_stages, int32_t* n_stages);
 NQS_API int64_t nqs_launch_count(void);

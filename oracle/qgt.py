@@ -92,6 +92,28 @@ def ntk_solve(dO: np.ndarray, e: np.ndarray, diag_shift: float, eta: float = 1.0
     return -eta * (np.conj(X).T @ np.linalg.solve(T, eps))
 
 
+def block_solve_sample_space(dO: np.ndarray, e: np.ndarray, block_off, diag_shift: float, eta: float = 1.0,
+                             w=None) -> np.ndarray:
+    """Per-block sample-space form of the block-layer update, for blocks with more
+    parameters than samples. With X_b = sqrt(w) dO_b (N_s x n_b) and eps = sqrt(w) e, the
+    block update -eta (X_b^H X_b + lambda I)^-1 X_b^H eps equals
+        dtheta_b = -eta X_b^H (X_b X_b^H + lambda I)^-1 eps
+    (push-through identity), which needs an N_s x N_s solve instead of an n_b x n_b one.
+    It is the block solve of Sec. 2 exactly when lambda > 0 and no eigenvalue is cut
+    (every eigenvalue of S_b + lambda I is at least lambda)."""
+    if not diag_shift > 0:
+        raise ValueError("the sample-space form needs a positive diagonal shift")
+    w = uniform_weights(dO.shape[0]) if w is None else np.asarray(w, dtype=np.float64)
+    sw = np.sqrt(w)
+    eps = sw * np.asarray(e, dtype=np.complex128)
+    out = np.empty(block_off[-1], dtype=np.complex128)
+    for b in range(len(block_off) - 1):
+        X = sw[:, None] * dO[:, block_off[b]:block_off[b + 1]]
+        T = X @ np.conj(X).T + diag_shift * np.eye(X.shape[0])
+        out[block_off[b]:block_off[b + 1]] = -eta * (np.conj(X).T @ np.linalg.solve(T, eps))
+    return out
+
+
 def sr_step(model, theta, configs, bond_ij, bond_j, block_off, diag_shift, cutoff,
             eta=1.0, c=1.0, sign_rule=1, w=None, absolute=False):
     """One block-layer SR step. Returns a dict of every intermediate."""

@@ -66,7 +66,7 @@ SIGNATURES = {
     "ntk_solve_workspace_size": (C.c_int, [I64, I64, I32, SZ]),
     "ntk_solve": (C.c_int, [P, I64, I64, I64, P, D, D, D, I32, P, P, P, P]),
     "nqs_shard_sums": (C.c_int, [P, I64, I64, I64, I32, P, P, P, P]),
-    "qgt_block_build_shard": (C.c_int, [P, I64, I64, I64, D, OFF, I32, P, P, P, I32, P, P, P, P]),
+    "qgt_block_build_shard": (C.c_int, [P, I64, I64, I64, I64, OFF, I32, P, P, P, I32, P, P, P, P, P, P]),
     "qgt_block_build": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P, P]),
     "qgt_block_build_static": (C.c_int, [P, I64, I64, I64, P, OFF, I32, P, I32, P, P, P, P, P]),
     "qgt_block_solve": (C.c_int, [P, OFF, I32, P, D, D, I32, D, I32, P, P, P, P, P]),
@@ -76,6 +76,7 @@ SIGNATURES = {
     "nqs_stage_timing": (C.c_int, [P, I32]),
     "nqs_stage_times": (C.c_int, [P, C.POINTER(C.c_double), I32, C.POINTER(C.c_int32)]),
     "nqs_launch_count": (C.c_int64, []),
+    "nqs_set_limits": (C.c_int, [I32, I64]),
 }
 
 _lib = None

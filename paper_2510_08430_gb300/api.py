@@ -38,6 +38,18 @@ def _ptr(t: Optional[torch.Tensor]) -> C.c_void_p:
     return C.c_void_p(0 if t is None else t.data_ptr())
 
 
+def _on(*tensors):
+    """Make the tensors' (common) device current for the library call, so that the
+    stream, the static scratch and every pointer belong to one device."""
+    devs = {t.device for t in tensors if t is not None}
+    if len(devs) != 1:
+        raise ValueError(f"arguments on several devices: {sorted(map(str, devs))}")
+    d = devs.pop()
+    if d.type != "cuda":
+        raise ValueError(f"arguments must be CUDA tensors, got {d}")
+    return torch.cuda.device(d)
+
+
 class Model:
     """Network description: kind (0 RBM, 1 FFNN) and widths."""
 
@@ -133,8 +145,9 @@ def nqs_jacobian(model: Model, theta: torch.Tensor, configs: torch.Tensor, preci
     ws.ensure(_size(lib.nqs_jacobian_workspace_size, C.byref(model.c), ns, p))
     logpsi = torch.empty(ns, dtype=torch.complex128, device=configs.device)
     O = torch.empty((n_p, ldo), dtype=_cdt(p), device=configs.device)
-    check(lib.nqs_jacobian(C.byref(model.c), _ptr(theta), _ptr(configs), ns, p, _ptr(logpsi), _ptr(O), ldo,
-                           ws.h, _stream()))
+    with _on(theta, configs):
+        check(lib.nqs_jacobian(C.byref(model.c), _ptr(theta), _ptr(configs), ns, p, _ptr(logpsi), _ptr(O), ldo,
+                               ws.h, _stream()))
     if sync:
         ws.sync_status()
     return logpsi, O
@@ -160,8 +173,9 @@ class NQSLogPsi(torch.autograd.Function):
         lib = _lib.load()
         g = grad_out.to(torch.complex128).contiguous()
         out = torch.empty(O.shape[0], dtype=torch.complex128, device=O.device)
-        check(lib.nqs_vjp(_ptr(O), int(O.shape[1]), ctx.n_s, int(O.shape[0]), _prec(ctx.precision), _ptr(g),
-                          _ptr(out), _stream()))
+        with _on(O, g):
+            check(lib.nqs_vjp(_ptr(O), int(O.shape[1]), ctx.n_s, int(O.shape[0]), _prec(ctx.precision), _ptr(g),
+                              _ptr(out), _stream()))
         return out, None, None, None
 
 
@@ -178,8 +192,9 @@ def nqs_local_energy(model: Model, theta: torch.Tensor, configs: torch.Tensor, h
     ws = ws or Workspace()
     ws.ensure(_size(lib.nqs_local_energy_workspace_size, C.byref(model.c), ns, C.byref(ham.c), p))
     eloc = torch.empty(ns, dtype=torch.complex128, device=configs.device)
-    check(lib.nqs_local_energy(C.byref(model.c), _ptr(theta), _ptr(configs), ns, C.byref(ham.c), p, _ptr(eloc),
-                               ws.h, _stream()))
+    with _on(theta, configs, ham.bond_ij):
+        check(lib.nqs_local_energy(C.byref(model.c), _ptr(theta), _ptr(configs), ns, C.byref(ham.c), p, _ptr(eloc),
+                                   ws.h, _stream()))
     if sync:
         ws.sync_status()
     return eloc
@@ -196,8 +211,9 @@ def nqs_connections(configs: torch.Tensor, ham: Hamiltonian, ws: Optional[Worksp
     off = torch.empty(ns + 1, dtype=torch.int64, device=configs.device)
     bond = torch.empty(max(maxc, 1), dtype=torch.int32, device=configs.device)
     n = C.c_int64(0)
-    check(lib.nqs_connections(_ptr(configs), ns, C.byref(ham.c), _ptr(cnt), _ptr(off), _ptr(bond), maxc,
-                              C.byref(n), ws.h, _stream()))
+    with _on(configs, ham.bond_ij):
+        check(lib.nqs_connections(_ptr(configs), ns, C.byref(ham.c), _ptr(cnt), _ptr(off), _ptr(bond), maxc,
+                                  C.byref(n), ws.h, _stream()))
     ws.sync_status()
     return cnt, off, bond[: n.value]
 
@@ -219,8 +235,9 @@ def qgt_block_build(O: torch.Tensor, n_s: int, block_off, eloc: torch.Tensor, pr
     F = torch.empty(n_p, dtype=torch.complex128, device=dev)
     Om = torch.empty(n_p, dtype=torch.complex128, device=dev)
     Em = torch.empty(1, dtype=torch.complex128, device=dev)
-    check(lib.qgt_block_build(_ptr(O), ldo, n_s, n_p, _ptr(w), off, nb, _ptr(eloc), p, _ptr(S), _ptr(F),
-                              _ptr(Om), _ptr(Em), ws.h, _stream()))
+    with _on(O, eloc, w):
+        check(lib.qgt_block_build(_ptr(O), ldo, n_s, n_p, _ptr(w), off, nb, _ptr(eloc), p, _ptr(S), _ptr(F),
+                                  _ptr(Om), _ptr(Em), ws.h, _stream()))
     if sync:
         ws.sync_status()
     return S, F, Om, Em
@@ -240,8 +257,9 @@ def qgt_block_build_static(O: torch.Tensor, n_s: int, block_off, eloc: torch.Ten
     F = torch.empty(n_p, dtype=torch.complex128, device=dev)
     Om = torch.empty(n_p, dtype=torch.complex128, device=dev)
     Em = torch.empty(1, dtype=torch.complex128, device=dev)
-    check(lib.qgt_block_build_static(_ptr(O), int(O.shape[1]), n_s, n_p, _ptr(w), off, nb, _ptr(eloc), p, _ptr(S),
-                                     _ptr(F), _ptr(Om), _ptr(Em), _stream()))
+    with _on(O, eloc, w):
+        check(lib.qgt_block_build_static(_ptr(O), int(O.shape[1]), n_s, n_p, _ptr(w), off, nb, _ptr(eloc), p,
+                                         _ptr(S), _ptr(F), _ptr(Om), _ptr(Em), _stream()))
     return S, F, Om, Em
 
 
@@ -259,8 +277,9 @@ def qgt_block_solve(S: torch.Tensor, block_off, F: torch.Tensor, diag_shift: flo
     dth = torch.empty(n_p, dtype=torch.complex128, device=dev)
     ev = torch.empty(n_p, dtype=torch.float64, device=dev) if want_evals else None
     nk = torch.empty(nb, dtype=torch.int32, device=dev)
-    check(lib.qgt_block_solve(_ptr(S), off, nb, _ptr(F), float(diag_shift), float(cutoff), int(cutoff_mode),
-                              float(eta), _solver(solver), _ptr(dth), _ptr(ev), _ptr(nk), ws.h, _stream()))
+    with _on(S, F):
+        check(lib.qgt_block_solve(_ptr(S), off, nb, _ptr(F), float(diag_shift), float(cutoff), int(cutoff_mode),
+                                  float(eta), _solver(solver), _ptr(dth), _ptr(ev), _ptr(nk), ws.h, _stream()))
     if sync:
         ws.sync_status()
     return dth, ev, nk
@@ -303,10 +322,11 @@ class SRStep:
 
     def __call__(self, theta: torch.Tensor, configs: torch.Tensor, sync: bool = False, _flags: int = 0):
         lib = _lib.load()
-        check(lib.sr_step(C.byref(self.model.c), _ptr(theta), _ptr(configs), self.n_s, C.byref(self.ham.c),
-                          self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p, self.solver,
-                          _ptr(self.dtheta), _ptr(self.emean), _ptr(self.evals), _ptr(self.n_kept),
-                          (NQS_SYNC if sync else 0) | _flags, self.ws.h, _stream()))
+        with _on(theta, configs, self.dtheta):
+            check(lib.sr_step(C.byref(self.model.c), _ptr(theta), _ptr(configs), self.n_s, C.byref(self.ham.c),
+                              self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p, self.solver,
+                              _ptr(self.dtheta), _ptr(self.emean), _ptr(self.evals), _ptr(self.n_kept),
+                              (NQS_SYNC if sync else 0) | _flags, self.ws.h, _stream()))
         return self.dtheta, self.emean
 
     def capture(self, theta: torch.Tensor, configs: torch.Tensor) -> "torch.cuda.CUDAGraph":
@@ -371,9 +391,10 @@ def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float
     em = torch.empty(n, dtype=torch.complex128, device=dev)
     ev = torch.empty(np_tot, dtype=torch.float64, device=dev) if want_evals else None
     nk = torch.empty(int(sum(len(o) - 1 for o in block_offs)), dtype=torch.int32, device=dev)
-    check(lib.sr_step_batched(n, mods, _ptr(th), _ptr(xc), ns, hs, off_c, nbs, float(diag_shift), float(cutoff),
-                              int(cutoff_mode), float(eta), p, _solver(solver), _ptr(dth), _ptr(em), _ptr(ev),
-                              _ptr(nk), NQS_SYNC, ws.h, _stream()))
+    with _on(th, xc):
+        check(lib.sr_step_batched(n, mods, _ptr(th), _ptr(xc), ns, hs, off_c, nbs, float(diag_shift), float(cutoff),
+                                  int(cutoff_mode), float(eta), p, _solver(solver), _ptr(dth), _ptr(em), _ptr(ev),
+                                  _ptr(nk), NQS_SYNC, ws.h, _stream()))
     sizes = [int(o[-1]) for o in block_offs]
     return list(torch.split(dth, sizes)), em, ev, nk
 
@@ -388,10 +409,18 @@ def ntk_solve(O: torch.Tensor, n_s: int, eloc: torch.Tensor, diag_shift: float, 
     ws = Workspace(_size(lib.ntk_solve_workspace_size, n_s, n_p, p), device=O.device)
     dth = torch.empty(n_p, dtype=torch.complex128, device=O.device)
     em = torch.empty(1, dtype=torch.complex128, device=O.device)
-    check(lib.ntk_solve(_ptr(O), int(O.shape[1]), n_s, n_p, _ptr(eloc), float(diag_shift), float(cutoff), float(eta),
-                        p, _ptr(dth), _ptr(em), ws.h, _stream()))
+    with _on(O, eloc):
+        check(lib.ntk_solve(_ptr(O), int(O.shape[1]), n_s, n_p, _ptr(eloc), float(diag_shift), float(cutoff),
+                            float(eta), p, _ptr(dth), _ptr(em), ws.h, _stream()))
     ws.sync_status()
     return dth, em
+
+
+def set_limits(max_sweeps: int = 0, wait_ns: int = 0) -> None:
+    """Test hook of the failure paths (nqs_set_limits): lower the eigen-solver and refinement
+    sweep limits and the device wait budget of the persistent solver kernels; 0 restores
+    the defaults."""
+    check(_lib.load().nqs_set_limits(int(max_sweeps), int(wait_ns)))
 
 
 def launch_count() -> int:

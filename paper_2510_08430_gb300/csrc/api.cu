@@ -27,6 +27,20 @@ unsigned long long& nqs::launch_counter() {
 }
 
 namespace {
+constexpr int QL_MAXIT_DEFAULT = 60;
+constexpr int REF_MAXIT_DEFAULT = 30;
+constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;
+std::atomic<int> g_ql_maxit{QL_MAXIT_DEFAULT};
+std::atomic<int> g_ref_maxit{REF_MAXIT_DEFAULT};
+std::atomic<unsigned long long> g_wait_ns{WAIT_NS_DEFAULT};
+}  // namespace
+
+nqs::Limits nqs::limits() {
+    return Limits{g_ql_maxit.load(std::memory_order_relaxed), g_ref_maxit.load(std::memory_order_relaxed),
+                  g_wait_ns.load(std::memory_order_relaxed)};
+}
+
+namespace {
 
 thread_local std::string g_err = "";
 
@@ -151,6 +165,7 @@ void plan_eloc(Arena& a, const ModelDesc& md, long long ns, int nbonds, ElocBufs
 
 struct BuildBufs {
     c128* e;
+    c128* means;  // global means of a sample-sharded step (n_p + 1)
     void* planes[5];
     double* diag;
     int8_t* gexp;
@@ -158,6 +173,7 @@ struct BuildBufs {
 };
 void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
     b->e = static_cast<c128*>(a.take(16 * ns));
+    b->means = static_cast<c128*>(a.take(16 * (np + 1)));
     b->ldk = round_up(ns, 64);
     const int nsp = nsplit_of(prec);
     for (int i = 0; i < 5; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
@@ -175,7 +191,7 @@ int run_model(const ModelDesc& md, int prec, const void* theta, const int8_t* x,
 
 int run_eloc(const ModelDesc& md, int prec, const HamDesc& hd, const int8_t* x, long long ns,
              const JacBufs& jb, const ElocBufs& eb, c128* eloc, DevStatus* status, cudaStream_t st) {
-    CK(launch_conn_count(x, ns, hd, eb.cnt, st), "conn_count");
+    CK(launch_conn_count(x, ns, hd, eb.cnt, status, st), "conn_count");
     CK(launch_scan(eb.cnt, ns, eb.off, st), "scan");
     CK(launch_conn_fill(x, ns, hd, eb.off, eb.cbond, eb.csamp, st), "conn_fill");
     if (prec == NQS_FP64) CK(launch_split_weights(md, jb.wtR, eb.wdf, st), "split_weights");
@@ -226,7 +242,7 @@ int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, 
     const size_t need = solve_workspace_bytes(off, nb);
     void* work = a.take(need);
     SolveArgs sa{shift, cutoff, eta, mode, evals != nullptr, solver != NQS_SOLVE_FP64, solver == NQS_SOLVE_MIXED_PSD,
-                 trd_event, trd_start, graph};
+                 trd_event, trd_start, graph, limits().ql_maxit};
     const int rc = launch_block_solve(S, off, nb, F, sa, dtheta, evals, n_kept, work, need, status, st);
     if (rc == NQS_ERR_UNSUPPORTED) return fail(rc, "block larger than the solver limit");
     if (rc != NQS_OK) return fail(rc, "block solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -298,6 +314,14 @@ int nqs_stage_times(nqs_workspace* ws, double* ms_out, int32_t max_stages, int32
         ms_out[i] = ms;
     }
     *n_stages = n;
+    return NQS_OK;
+}
+
+int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns) {
+    if (max_sweeps < 0 || wait_ns < 0) return fail(NQS_ERR_INVALID_ARG, "nqs_set_limits: negative limit");
+    g_ql_maxit.store(max_sweeps ? max_sweeps : QL_MAXIT_DEFAULT);
+    g_ref_maxit.store(max_sweeps ? max_sweeps : REF_MAXIT_DEFAULT);
+    g_wait_ns.store(wait_ns ? (unsigned long long)wait_ns : WAIT_NS_DEFAULT);
     return NQS_OK;
 }
 
@@ -478,7 +502,7 @@ int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h
     rc = check_ws(ws, a);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(launch_conn_count(configs, n_s, hd, conn_count, st), "conn_count");
+    CK(launch_conn_count(configs, n_s, hd, conn_count, status_of(ws), st), "conn_count");
     CK(launch_scan(conn_count, n_s, reinterpret_cast<long long*>(conn_offset), st), "scan");
     long long total = 0;
     CK(cudaMemcpyAsync(&total, conn_offset + n_s, sizeof total, cudaMemcpyDeviceToHost, st), "total read");
@@ -519,13 +543,15 @@ int nqs_shard_sums(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t
     return NQS_OK;
 }
 
-int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, double weight, const int64_t* block_off,
-                          int32_t n_blocks, const void* eloc, const void* Omean_in, const void* Emean_in,
-                          int32_t precision, void* S_packed, void* F_out, nqs_workspace* ws, void* stream) {
+int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, int64_t n_total, const int64_t* block_off,
+                          int32_t n_blocks, const void* eloc, const void* Osum_in, const void* Esum_in,
+                          int32_t precision, void* S_packed, void* F_out, void* Omean_out, void* Emean_out,
+                          nqs_workspace* ws, void* stream) {
     if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
-    if (!O || !eloc || !Omean_in || !Emean_in || !S_packed || !F_out || n_s < 1 || n_p < 1 || ldo < n_s ||
-        !(weight > 0.0))
+    if (!O || !eloc || !Osum_in || !Esum_in || !S_packed || !F_out || n_s < 1 || n_p < 1 || ldo < n_s ||
+        n_total < n_s)
         return fail(NQS_ERR_INVALID_ARG, "qgt_block_build_shard: bad arguments");
+    const double weight = 1.0 / (double)n_total;
     int rc = check_offsets(block_off, n_blocks, n_p);
     if (rc) return rc;
     Arena a = arena_of(ws);
@@ -537,10 +563,16 @@ int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p, double
     DevStatus* status = status_of(ws);
     const int nsp = nsplit_of(precision);
     c128* S = static_cast<c128*>(S_packed);
-    CK(launch_ecenter(static_cast<const c128*>(eloc), n_s, static_cast<const c128*>(Emean_in), bb.e, st), "ecenter");
+    CK(launch_sums_to_means(static_cast<const c128*>(Osum_in), static_cast<const c128*>(Esum_in), n_p, n_total,
+                            bb.means, st),
+       "means");
+    if (Omean_out)
+        CK(cudaMemcpyAsync(Omean_out, bb.means, 16 * (size_t)n_p, cudaMemcpyDeviceToDevice, st), "mean copy");
+    if (Emean_out)
+        CK(cudaMemcpyAsync(Emean_out, bb.means + n_p, 16, cudaMemcpyDeviceToDevice, st), "mean copy");
+    CK(launch_ecenter(static_cast<const c128*>(eloc), n_s, bb.means + n_p, bb.e, st), "ecenter");
     CK(launch_center(precision, nsp, O, ldo, n_s, n_p, nullptr, bb.e, static_cast<c128*>(F_out), nullptr,
-                     nsp ? bb.planes : nullptr, bb.ldk, bb.diag, bb.gexp, n_p, status, st,
-                     static_cast<const c128*>(Omean_in), weight),
+                     nsp ? bb.planes : nullptr, bb.ldk, bb.diag, bb.gexp, n_p, status, st, bb.means, weight),
        "center");
     GramTable* tab = new (std::nothrow) GramTable;
     if (!tab) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
@@ -946,18 +978,29 @@ namespace {
 constexpr int STATIC_MAX_DEVICES = 64;
 std::atomic<c128*> g_static_e_addr[STATIC_MAX_DEVICES];  // device address of g_static_e, per device
 
-// Set-up, once per device with that device current: look up where g_static_e lives.
-int static_scratch(c128** out) {
+// Device address of g_static_e on the current device. The address is looked up again on
+// every call whose stream is not capturing (cheap), so a device reset or a re-created
+// primary context cannot leave a stale address behind. During stream capture the address
+// cached by the last uncaptured call on this device is used, so the first call on a device
+// must come before any capture.
+int static_scratch(cudaStream_t st, c128** out) {
     int dev = -1;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= STATIC_MAX_DEVICES)
         return fail(NQS_ERR_UNSUPPORTED, "device ordinal %d beyond %d", dev, STATIC_MAX_DEVICES);
-    c128* p = g_static_e_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap), "cudaStreamIsCapturing");
+    c128* p = nullptr;
+    if (cap == cudaStreamCaptureStatusNone) {
         void* q = nullptr;
         CK(cudaGetSymbolAddress(&q, g_static_e), "cudaGetSymbolAddress");
         p = static_cast<c128*>(q);
         g_static_e_addr[dev].store(p, std::memory_order_release);
+    } else {
+        p = g_static_e_addr[dev].load(std::memory_order_acquire);
+        if (!p)
+            return fail(NQS_ERR_INVALID_ARG,
+                        "qgt_block_build_static: first call on device %d made during stream capture", dev);
     }
     *out = p;
     return NQS_OK;
@@ -979,10 +1022,10 @@ extern "C" int qgt_block_build_static(void* O, int64_t ldo, int64_t n_s, int64_t
                     (long long)n_s, NQS_STATIC_MAX_SAMPLES);
     int rc = check_offsets(block_off, n_blocks, n_p);
     if (rc) return rc;
-    c128* e = nullptr;
-    rc = static_scratch(&e);
-    if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c128* e = nullptr;
+    rc = static_scratch(st, &e);
+    if (rc) return rc;
     CK(launch_emean(static_cast<const c128*>(eloc), w, n_s, static_cast<c128*>(Emean_out), e, nullptr, st), "emean");
     CK(launch_center(precision, 0, O, ldo, n_s, n_p, w, e, static_cast<c128*>(F_out), static_cast<c128*>(Omean_out),
                      nullptr, 0, nullptr, nullptr, n_p, nullptr, st),

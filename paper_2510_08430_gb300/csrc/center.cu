@@ -55,6 +55,23 @@ cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long 
     return cudaGetLastError();
 }
 
+// Global means of a sample-sharded step from the all-reduced shard sums:
+// means[k] = osum[k] / n_total (k < n_p), means[n_p] = esum[0] / n_total.
+__global__ void sums_to_means_kernel(const c128* __restrict__ osum, const c128* __restrict__ esum, long long np,
+                                     double inv_n, c128* __restrict__ means) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k <= np; k += (long long)gridDim.x * blockDim.x)
+        means[k] = inv_n * (k < np ? osum[k] : esum[0]);
+}
+
+cudaError_t launch_sums_to_means(const c128* osum, const c128* esum, long long np, long long n_total, c128* means,
+                                 cudaStream_t st) {
+    count_launch();
+    const long long g = (np + 256) / 256;
+    sums_to_means_kernel<<<(unsigned)(g < 1024 ? g : 1024), 256, 0, st>>>(osum, esum, np, 1.0 / (double)n_total,
+                                                                           means);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st) {
     count_launch();
     ecenter_kernel<<<(unsigned)((ns + 255) / 256 < 1024 ? (ns + 255) / 256 : 1024), 256, 0, st>>>(eloc, ns, emean, e);

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(512) ql_solve_kernel(SolveBufs B, int nb, Solv
         ee[n - 1] = 0.0;
     }
     __syncthreads();
-    const int maxit = 60;
+    const int maxit = a.ql_maxit;
     for (int l = 0; l < n; ++l) {
         int iter = 0;
         while (true) {

@@ -57,7 +57,6 @@ template <typename R> struct TrdBufs {
 };
 
 constexpr int QNB = 32;      // reflectors per panel of the blocked (WY) application of Q
-constexpr int REF_MAXIT = 30;
 constexpr double REF_TOL = 1e-14;
 
 struct MixBufs {

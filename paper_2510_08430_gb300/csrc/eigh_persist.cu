@@ -26,7 +26,6 @@ namespace nqs {
 namespace {
 
 constexpr int PT = 256;                              // threads per CTA (== CH)
-constexpr unsigned long long BAR_NS = 2000000000ull; // budget of one grid-wide wait
 
 static_assert(PT == CH, "one thread per row of a chunk");
 static_assert(MAXB <= PT, "unit prefix holds one block per thread");
@@ -39,8 +38,8 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 // Grid barrier over all CTAs of the launch: bar[0] counts arrivals, bar[1] is the
 // generation. The last arriver resets the count and advances the generation. A wait
-// that exceeds BAR_NS records NQS_ERR_TIMEOUT and returns false; the caller returns.
-__device__ bool grid_sync(unsigned* bar, DevStatus* status, int where, int* ok_s) {
+// that exceeds `budget` ns records NQS_ERR_TIMEOUT and returns false; the caller returns.
+__device__ bool grid_sync(unsigned* bar, DevStatus* status, int where, int* ok_s, unsigned long long budget) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* gen = bar + 1;
@@ -55,7 +54,7 @@ __device__ bool grid_sync(unsigned* bar, DevStatus* status, int where, int* ok_s
             const unsigned long long t0 = now_ns();
             while (*gen == g) {
                 __nanosleep(64);
-                if (now_ns() - t0 > BAR_NS) {
+                if (now_ns() - t0 > budget) {
                     ok = 0;
                     set_status(status, NQS_ERR_TIMEOUT, where, -1);
                     break;
@@ -376,7 +375,7 @@ template <> struct TrdOcc<float> { static constexpr int value = 3; };  // FP32: 
 
 template <typename R>
 __global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBufs<R> B, int nb, int nmax, unsigned* bar,
-                                                             DevStatus* status) {
+                                                             DevStatus* status, unsigned long long wait_ns) {
     __shared__ int sn[MAXB];
     __shared__ long long pref[MAXB + 1];
     __shared__ long long wsum[PT / 32];
@@ -392,7 +391,7 @@ __global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBu
         const int b = unit_block(pref, nb, u);
         trd_prologue<R>(B, b, (int)(u - pref[b]));
     }
-    if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+    if (!grid_sync(bar, status, W_TRD, &ok_s, wait_ns)) return;
     for (int j = 0; j < nmax; ++j) {
         cx<R>* vcur = (j & 1) ? B.v1 : B.v0;
         const cx<R>* vprev = (j & 1) ? B.v0 : B.v1;
@@ -402,7 +401,7 @@ __global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBu
             const int b = unit_block(pref, nb, u);
             trd_phase_r<R>(B, b, j, (int)(u - pref[b]), vprev, vcur, shd, shc, status);
         }
-        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+        if (!grid_sync(bar, status, W_TRD, &ok_s, wait_ns)) return;
         tot = unit_prefix(
             nb,
             [&](int b) -> long long {
@@ -415,14 +414,14 @@ __global__ void __launch_bounds__(PT, TrdOcc<R>::value) trd_persist_kernel(TrdBu
             const int b = unit_block(pref, nb, u);
             trd_phase_c<R>(B, b, j, u - pref[b], vprev, vcur, sm);
         }
-        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+        if (!grid_sync(bar, status, W_TRD, &ok_s, wait_ns)) return;
         tot = unit_prefix(
             nb, [&](int b) -> long long { return sn[b] - 2 >= j ? (sn[b] - j - 1 + DCH - 1) / DCH : 0; }, pref, wsum);
         for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
             const int b = unit_block(pref, nb, u);
             trd_phase_x<R>(B, b, j, (int)(u - pref[b]), vcur, red, shd, shc);
         }
-        if (!grid_sync(bar, status, W_TRD, &ok_s)) return;
+        if (!grid_sync(bar, status, W_TRD, &ok_s, wait_ns)) return;
     }
 }
 
@@ -587,7 +586,8 @@ __device__ void ref_hemv_tile(const MixBufs& M, const EBlk& blk, long long t, Re
 
 __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixBufs M, int nb, int pmaxall,
                                                                 const c128* F, double shift, unsigned* bar,
-                                                                DevStatus* status) {
+                                                                DevStatus* status, int maxit,
+                                                                unsigned long long wait_ns) {
     __shared__ int sn[MAXB];
     __shared__ long long cbase[MAXB + 1];  // prefix of row chunks over slots (pdot rows)
     __shared__ int sdone[MAXB];
@@ -625,11 +625,11 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
         s = block_sum(s, shd);
         if (tid == 0) M.fn[b] = s;
     }
-    if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+    if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
     for (int b = tid; b < nb; b += PT) sdone[b] = (M.fn[b] == 0.0) ? 1 : 0;
     __syncthreads();
 
-    for (int it = 0; it < REF_MAXIT; ++it) {
+    for (int it = 0; it < maxit; ++it) {
         int open = 0;
         for (int b = tid; b < nb; b += PT) open |= !sdone[b];
         if (!__syncthreads_or(open)) break;
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
             __syncthreads();
             panel_apply(M, blk, b, cbase[b], totch, c, -1, true, n_panels(blk.n) > 0 ? 0 : -1, M.y32, 1, sm);
         }
-        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
         for (int s = 0; s < pmaxall; ++s) {
             tot = unit_prefix(
                 nb, [&](int b) -> long long { return (!sdone[b] && s < n_panels(sn[b])) ? chunks(b) : 0; }, pref,
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
                 const int q = s + 1 < n_panels(blk.n) ? s + 1 : -1;
                 panel_apply(M, blk, b, cbase[b], totch, (int)(u - pref[b]), s, true, q, M.y32, s & 1, sm);
             }
-            if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+            if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
         }
 
         // ---- w = (T + lambda I)^{-1} y by the LDL^T factors (one thread per block)
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
                 w[k] = ccast<float>(z);
             }
         }
-        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
 
         // ---- x += Q w: panels pmax-1 .. 0 with T
         tot = unit_prefix(nb, [&](int b) -> long long { return sdone[b] ? 0 : chunks(b); }, pref, wsum);
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
             const int r = c * CH + tid;
             if (np_b == 0 && r < blk.n) M.x[blk.off + r] = M.x[blk.off + r] + ccast<double>(M.w32[blk.off + r]);
         }
-        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
         for (int s = 0; s < pmaxall; ++s) {
             tot = unit_prefix(
                 nb, [&](int b) -> long long { return (!sdone[b] && s < n_panels(sn[b])) ? chunks(b) : 0; }, pref,
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
                 const int r = c * CH + tid;
                 if (p == 0 && r < blk.n) M.x[blk.off + r] = M.x[blk.off + r] + ccast<double>(M.w32[blk.off + r]);
             }
-            if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+            if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
         }
 
         // ---- FP64 residual r = F - (S + lambda I) x
@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
             const int b = unit_block(pref, nb, u);
             ref_hemv_tile(M, B.tab[b], u - pref[b], sm);
         }
-        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
         tot = unit_prefix(
             nb, [&](int b) -> long long { return sdone[b] ? 0 : (sn[b] + DCH - 1) / DCH; }, pref, wsum);
         for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
             }
             __syncthreads();
         }
-        if (!grid_sync(bar, status, W_SOLVE, &ok_s)) return;
+        if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
 
         // ---- convergence (every CTA decides the same from the same partials)
         for (int b = tid >> 5; b < nb; b += PT / 32) {  // one warp per block
@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
                     sdone[b] = 1;
                 } else if (blockIdx.x == 0) {
                     if (!isfinite(s)) set_status(status, NQS_ERR_NONFINITE, W_SOLVE, B.tab[b].orig);
-                    else if (it == REF_MAXIT - 1) set_status(status, NQS_ERR_NOT_CONVERGED, W_SOLVE, B.tab[b].orig);
+                    else if (it == maxit - 1) set_status(status, NQS_ERR_NOT_CONVERGED, W_SOLVE, B.tab[b].orig);
                 }
             }
         }
@@ -809,7 +809,8 @@ int launch_trd_persist(const TrdBufs<R>& B, const EBTab& tab, unsigned* bar, Dev
     if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return NQS_ERR_CUDA;
     TrdBufs<R> Bc = B;
     int nb = tab.nb;
-    void* args[] = {&Bc, &nb, &nmax, &bar, &status};
+    unsigned long long wait_ns = limits().wait_ns;
+    void* args[] = {&Bc, &nb, &nmax, &bar, &status, &wait_ns};
     count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PT), args, 0, st) == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
 }
@@ -831,7 +832,10 @@ int launch_refine_persist(const SolveBufs& B, const MixBufs& M, const EBTab& tab
     SolveBufs Bc = B;
     MixBufs Mc = M;
     int nb = tab.nb;
-    void* args[] = {&Bc, &Mc, &nb, &pmax, (void*)&F, &shift, &bar, &status};
+    const Limits lim = limits();
+    int maxit = lim.ref_maxit;
+    unsigned long long wait_ns = lim.wait_ns;
+    void* args[] = {&Bc, &Mc, &nb, &pmax, (void*)&F, &shift, &bar, &status, &maxit, &wait_ns};
     count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PT), args, 0, st) == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
 }

@@ -12,13 +12,33 @@ namespace nqs {
 
 constexpr int CONN_WARPS = 8;
 
+// Bond (i, j) as read from the caller's table; a bond with i == j or an index outside
+// [0, N) becomes (-1, -1), which no stage treats as anti-aligned or reads spins for.
+__device__ __forceinline__ int2 checked_bond(const int32_t* __restrict__ bij, int b, int N, bool* bad) {
+    const int i = bij[2 * b], j = bij[2 * b + 1];
+    if (i < 0 || i >= N || j < 0 || j >= N || i == j) {
+        *bad = true;
+        return make_int2(-1, -1);
+    }
+    return make_int2(i, j);
+}
+__device__ __forceinline__ bool anti_aligned(const int8_t* row, int2 bd) {
+    return bd.x >= 0 && row[bd.x] != row[bd.y];
+}
+
+// Counts the anti-aligned bonds of every sample; also validates the bond table and
+// records NQS_ERR_INVALID_ARG (detail: first bad bond index seen) for a bad bond.
 __global__ void __launch_bounds__(256) conn_count_kernel(const int8_t* __restrict__ x, long long ns,
                                                           int N, int nb, const int32_t* __restrict__ bij,
-                                                          int32_t* __restrict__ cnt) {
+                                                          int32_t* __restrict__ cnt, DevStatus* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int2* bonds = reinterpret_cast<int2*>(smem_raw);
     int8_t* rowbuf = reinterpret_cast<int8_t*>(bonds + nb);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) bonds[b] = make_int2(bij[2 * b], bij[2 * b + 1]);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        bool bad = false;
+        bonds[b] = checked_bond(bij, b, N, &bad);
+        if (bad && blockIdx.x == 0) set_status(status, NQS_ERR_INVALID_ARG, W_ELOC, b);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int8_t* row = rowbuf + wid * N;
@@ -29,7 +49,7 @@ __global__ void __launch_bounds__(256) conn_count_kernel(const int8_t* __restric
         for (int b0 = 0; b0 < nb; b0 += 32) {
             const int b = b0 + lane;
             bool anti = false;
-            if (b < nb) anti = row[bonds[b].x] != row[bonds[b].y];
+            if (b < nb) anti = anti_aligned(row, bonds[b]);
             total += __popc(__ballot_sync(0xffffffffu, anti));
         }
         if (lane == 0) cnt[s] = total;
@@ -44,7 +64,10 @@ __global__ void __launch_bounds__(256) conn_fill_kernel(const int8_t* __restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int2* bonds = reinterpret_cast<int2*>(smem_raw);
     int8_t* rowbuf = reinterpret_cast<int8_t*>(bonds + nb);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) bonds[b] = make_int2(bij[2 * b], bij[2 * b + 1]);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        bool bad = false;
+        bonds[b] = checked_bond(bij, b, N, &bad);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int8_t* row = rowbuf + wid * N;
@@ -55,7 +78,7 @@ __global__ void __launch_bounds__(256) conn_fill_kernel(const int8_t* __restrict
         for (int b0 = 0; b0 < nb; b0 += 32) {
             const int b = b0 + lane;
             bool anti = false;
-            if (b < nb) anti = row[bonds[b].x] != row[bonds[b].y];
+            if (b < nb) anti = anti_aligned(row, bonds[b]);
             const unsigned m = __ballot_sync(0xffffffffu, anti);
             if (anti) {
                 const long long at = pos + __popc(m & ((1u << lane) - 1u));
@@ -556,6 +579,8 @@ __global__ void eloc_reduce_kernel(const int8_t* __restrict__ x, long long ns, H
     const int8_t* row = x + s * h.n_sites;
     for (int b = 0; b < h.n_bonds; ++b) {
         const int i = h.bond_ij[2 * b], j = h.bond_ij[2 * b + 1];
+        // a bad bond was reported by conn_count_kernel; it contributes nothing here
+        if (i < 0 || i >= h.n_sites || j < 0 || j >= h.n_sites || i == j) continue;
         diag += h.bond_J[b] * (double)(row[i] * row[j]);
     }
     c128 e = mk<double>(h.c * diag, 0.0);
@@ -573,14 +598,15 @@ static int conn_grid(long long ns) {
     return (int)(g < 8192 ? (g < 1 ? 1 : g) : 8192);
 }
 
-cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, int32_t* cnt,
+cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, int32_t* cnt, DevStatus* status,
                               cudaStream_t st) {
     if (ns <= 0) return cudaSuccess;
     const size_t sm = conn_smem(h);
     cudaError_t e = cudaFuncSetAttribute(conn_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
-    conn_count_kernel<<<conn_grid(ns), 32 * CONN_WARPS, sm, st>>>(x, ns, h.n_sites, h.n_bonds, h.bond_ij, cnt);
+    conn_count_kernel<<<conn_grid(ns), 32 * CONN_WARPS, sm, st>>>(x, ns, h.n_sites, h.n_bonds, h.bond_ij, cnt,
+                                                                  status);
     return cudaGetLastError();
 }
 cudaError_t launch_scan(const int32_t* cnt, long long ns, long long* off, cudaStream_t st) {

@@ -50,7 +50,9 @@ struct HamDesc {
     double c;
     int sign_rule;
 };
-cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, int32_t* cnt,
+// validates the bonds (0 <= i, j < n_sites, i != j): a bad bond records NQS_ERR_INVALID_ARG
+// in `status` and is skipped by every later stage
+cudaError_t launch_conn_count(const int8_t* x, long long ns, const HamDesc& h, int32_t* cnt, DevStatus* status,
                               cudaStream_t st);
 cudaError_t launch_scan(const int32_t* cnt, long long ns, long long* off, cudaStream_t st);
 cudaError_t launch_conn_fill(const int8_t* x, long long ns, const HamDesc& h, const long long* off,
@@ -75,6 +77,9 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long ns, long long np, const c128* eloc,
                               c128* osum, c128* esum, cudaStream_t st);
 cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st);
+// means[0..np) = osum / n_total, means[np] = esum[0] / n_total (global means of a sharded step)
+cudaError_t launch_sums_to_means(const c128* osum, const c128* esum, long long np, long long n_total, c128* means,
+                                 cudaStream_t st);
 // sample-space (NTK) comparator
 cudaError_t launch_ntk_transpose(int prec, const c128* O, long long ldo, long long ns, long long np, void* Y,
                                  long long ldy, cudaStream_t st);
@@ -115,6 +120,17 @@ void gram_table(const int64_t* block_off, int nb, int tile_rows, GramTable* tab)
 // overwrite the diagonal of every S_b with diag (FP64 sums of |dO_k|^2)
 cudaError_t launch_set_diag(c128* S, const GramTable& tab, const double* diag, cudaStream_t st);
 
+// ---- iteration limits and device wait budget ----
+// Defaults: 60 implicit-QL sweeps per eigenvalue, 30 refinement sweeps, 2 s per device-side
+// wait. nqs_set_limits (a test hook) lowers them so that the failure paths can be driven
+// on purpose: a limit that runs out records NQS_ERR_NOT_CONVERGED or NQS_ERR_TIMEOUT.
+struct Limits {
+    int ql_maxit;
+    int ref_maxit;
+    unsigned long long wait_ns;
+};
+Limits limits();
+
 // ---- per-block solve ----
 struct SolveArgs {
     double shift, cutoff, eta;
@@ -125,6 +141,7 @@ struct SolveArgs {
     cudaEvent_t ev_trd_done;    // recorded after the tridiagonal reduction (or NULL)
     cudaEvent_t ev_trd_start;   // recorded just before the tridiagonal reduction (or NULL)
     bool no_host_sync;          // capturable: the mixed certificate is checked on the device
+    int ql_maxit;               // implicit-QL sweep limit per eigenvalue
 };
 size_t solve_workspace_bytes(const int64_t* block_off, int nb);
 int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,

@@ -91,11 +91,14 @@ def test_newer_entry_points_validate_on_the_host(lib):
     # NTK: split precisions are not an NTK Gram option
     assert lib.ntk_solve_workspace_size(64, 100, _lib.NQS_SPLIT_BF16_EXACT, C.byref(out)) == -1
     assert lib.ntk_solve_workspace_size(64, 100, _lib.NQS_FP32, C.byref(out)) == 0 and out.value > 64 * 64 * 16
-    # shard build: weight must be positive
+    # shard build: the total sample count cannot be below the shard's
     off = (C.c_int64 * 2)(0, 10)
-    assert lib.qgt_block_build_shard(fake, 64, 64, 10, 0.0, off, 1, fake, fake, fake, 0, fake, fake, None,
-                                     None) == -1
+    assert lib.qgt_block_build_shard(fake, 64, 64, 10, 63, off, 1, fake, fake, fake, 0, fake, fake, None, None,
+                                     None, None) == -1
     assert b"qgt_block_build_shard" in lib.nqs_last_error()
+    # test hook: negative limits are rejected, zeros restore the defaults
+    assert lib.nqs_set_limits(-1, 0) == -1 and lib.nqs_set_limits(0, -5) == -1
+    assert lib.nqs_set_limits(0, 0) == 0
     # shard sums and VJP: leading dimension below n_s
     assert lib.nqs_shard_sums(fake, 10, 64, 10, 0, fake, fake, fake, None) == -1
     assert lib.nqs_vjp(fake, 10, 64, 10, 0, fake, fake, None) == -1

@@ -159,3 +159,34 @@ def test_sample_permutation_and_duplication_invariance():
             np.testing.assert_allclose(a, b, atol=1e-13)
         np.testing.assert_allclose(F1, F0, atol=1e-13)
         np.testing.assert_allclose(d1, d0, rtol=1e-8, atol=1e-9 * np.linalg.norm(d0))
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_block_sample_space_solve_equals_block_solve(weighted):
+    """Per-block push-through identity: for every block, the N_s x N_s sample-space solve
+    equals the n_b x n_b eigen-decomposition solve when no eigenvalue is cut; blocks both
+    wider (408, 200 parameters) and narrower (9) than the 100 samples."""
+    model = W.Model(W.FFNN, (16, 24, 8, 1))
+    rng = np.random.default_rng(21)
+    theta = W.init_params(model, rng)
+    x = W.zero_sz_configs(16, 100, rng)
+    ij, jj = W.square_j1j2_bonds(4, 4, 1.0, 0.4)
+    _, O = nqs.jacobian(model, theta, x)
+    el = hamiltonian.local_energy(model, theta, x, ij, jj)
+    w = None
+    if weighted:
+        r = rng.random(100) + 0.05
+        w = r / r.sum()
+    _, _, dO, e = qgt.center(O, el, w)
+    F = qgt.force(dO, e, w)
+    off = model.block_offsets()
+    S = qgt.block_qgt(dO, off, w)
+    lam = 3e-3
+    ref, sig, kept = qgt.block_solve(S, F, off, lam, 1e-12, eta=0.7)
+    assert all(k == n for k, n in zip(kept, np.diff(off)))
+    d = qgt.block_solve_sample_space(dO, e, off, lam, eta=0.7, w=w)
+    for b in range(len(off) - 1):
+        sl = slice(off[b], off[b + 1])
+        np.testing.assert_allclose(d[sl], ref[sl], rtol=0, atol=1e-10 * np.linalg.norm(ref[sl]))
+    with pytest.raises(ValueError):
+        qgt.block_solve_sample_space(dO, e, off, 0.0)

@@ -81,5 +81,22 @@ def test_static_build_matches_workspace_build_on_consecutive_calls(prec, tol):
 
 @pytest.mark.gpu
 def test_static_build_at_its_sample_limit():
+    """At the largest sample count the static scratch holds: against the workspace build and,
+    on its own, against the FP64 oracle (weighted means, centring, force and block QGT)."""
+    import oracle
+    import paper_2510_08430_gb300 as nq
     from paper_2510_08430_gb300 import _lib as L
-    _compare(*_inputs("chain10_rbm", L.NQS_STATIC_MAX_SAMPLES, "fp64", True), "fp64", 1e-13)
+    ns = L.NQS_STATIC_MAX_SAMPLES
+    w, O, el, ws = _inputs("chain10_rbm", ns, "fp64", True)
+    _compare(w, O, el, ws, "fp64", 1e-13)
+    S, F, Om, Em = nq.qgt_block_build_static(O.clone(), ns, w.block_off, el, "fp64", w=ws)
+    wt = ws.cpu().numpy()
+    _, Oo = oracle.nqs.jacobian(w.model, w.theta, w.configs)
+    elo = oracle.hamiltonian.local_energy(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.c, w.sign_rule)
+    e_mean, o_mean, dO, e = oracle.qgt.center(Oo, elo, wt)
+    assert rel(F.cpu().numpy(), oracle.qgt.force(dO, e, wt)) < 1e-11
+    assert rel(Om.cpu().numpy(), o_mean) < 1e-12
+    assert abs(Em.cpu().numpy()[0] - e_mean) < 1e-12 * abs(e_mean)
+    Sg = unpack_lower(S.cpu().numpy(), w.block_off)
+    for b, Sb in enumerate(oracle.qgt.block_qgt(dO, w.block_off, wt)):
+        assert rel(Sg[b], np.tril(Sb)) < 1e-12, b
