@@ -288,7 +288,19 @@ NQS_API int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p
  *                  a Gram matrix (positive semi-definite up to a rounding of at most
  *                  1e-6 sigma_max, as qgt_block_build produces), so sigma_min >= shift -
  *                  1e-6 sigma_max certifies the cutoff. sr_step uses this certificate when
- *                  called with NQS_SOLVE_MIXED. */
+ *                  called with NQS_SOLVE_MIXED.
+ *                  When no eigenvalues are requested (evals_out NULL) and every block has at
+ *                  most 65536 parameters, the cutoff is first certified without an
+ *                  eigen-decomposition: sigma_max(S~_b) <= ||S_b||_F + shift, sigma_min(S~_b)
+ *                  >= shift - 1e-6 ||S_b||_F, and every eigenvalue is kept when the lower bound
+ *                  exceeds cutoff * upper bound (relative mode) or cutoff (absolute mode).
+ *                  Certified blocks are then solved as the positive-definite system
+ *                  S~_b x = F_b: FP32 tiled Cholesky of S~_b and FP64-residual iterative
+ *                  refinement until ||F - S~ x|| <= 1e-14 ||F||; dtheta_b = -eta x equals the
+ *                  pseudo-inverse update up to rounding. A block that is not certified, meets
+ *                  a non-positive FP32 pivot or does not converge sends every block to the
+ *                  eigen-decomposition path above (one more host synchronisation); under
+ *                  NQS_GRAPH that is recorded as NQS_ERR_RETRY instead. */
 enum { NQS_SOLVE_FP64 = 0, NQS_SOLVE_MIXED = 1, NQS_SOLVE_MIXED_PSD = 2 };
 
 /* qgt_block_solve -- per-block shifted pseudo-inverse solve (Sec. 2):
@@ -358,8 +370,10 @@ NQS_API int sr_step_batched(int32_t n_inst, const nqs_model* models, const void*
  * nqs_stage_timing(ws, 1) makes later sr_step calls on `ws` record CUDA events
  * on their stream at the stage boundaries: [0] Jacobian (parameter conversion,
  * forward, backward, O write), [1] local energies, [2] means/centring/force,
- * [3] block Gram (plus the solver's set-up copies), [4] Householder tridiagonal
- * reduction (exactly its one kernel), [5] eigenvalues, solve and back-transform. nqs_stage_times synchronises on the last event and
+ * [3] block Gram (plus the solver's set-up copies and, on the Cholesky path, the FP32 tile
+ * copy and certificate), [4] factorization: the FP32 tiled Cholesky panels of the Gram-matrix
+ * path, or the Householder tridiagonal reduction (exactly its one kernel) of the eigen path,
+ * [5] refinement, eigenvalues, solve and back-transform. nqs_stage_times synchronises on the last event and
  * returns the milliseconds of each stage of the most recent timed sr_step.
  * nqs_launch_count returns the number of kernels this library has launched in
  * the process (all threads). */

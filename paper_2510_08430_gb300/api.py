@@ -308,7 +308,7 @@ class SRStep:
         self.evals = torch.empty(self.n_p, dtype=torch.float64, device=device) if want_evals else None
         self.n_kept = torch.empty(self.nb, dtype=torch.int32, device=device)
 
-    STAGES = ("jacobian", "local_energy", "centring_force", "gram", "tridiagonal_reduction", "solve")
+    STAGES = ("jacobian", "local_energy", "centring_force", "gram", "factorization", "solve")
 
     def enable_stage_timing(self, on: bool = True) -> None:
         check(_lib.load().nqs_stage_timing(self.ws.h, 1 if on else 0))

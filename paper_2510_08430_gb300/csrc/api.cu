@@ -178,7 +178,7 @@ void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
     const int nsp = nsplit_of(prec);
     for (int i = 0; i < 5; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
     b->diag = nsp ? static_cast<double*>(a.take(8 * np)) : nullptr;
-    b->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(b->ldk / 16) * np)) : nullptr;
+    b->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(b->ldk / GRAM_GROUP) * np)) : nullptr;
 }
 
 // ------------------------------------------------------------------ stages
@@ -818,7 +818,7 @@ void plan_batch_bufs(Arena& a, const BatchPlan& bp, int prec, BatchBufs* bb) {
     const int nsp = nsplit_of(prec);
     for (int q = 0; q < 5; ++q) bb->planes[q] = q < nsp ? a.take(2ull * 2 * bp.np_tot * bp.ldk) : nullptr;
     bb->diag = nsp ? static_cast<double*>(a.take(8 * (size_t)bp.np_tot)) : nullptr;
-    bb->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(bp.ldk / 16) * bp.np_tot)) : nullptr;
+    bb->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(bp.ldk / GRAM_GROUP) * bp.np_tot)) : nullptr;
 }
 
 }  // namespace

@@ -716,7 +716,10 @@ static SolveLayoutAll layout_all(const int64_t* off, int nb) {
     }
     size_t p = A.L.total;
     auto take = [&](size_t bytes) { size_t at = p; p += al(bytes); return at; };
-    A.sf = take(8ull * sq);
+    // the FP32 copy of the eigen path and the Cholesky path's buffers share one region: the
+    // eigen path runs only after the Cholesky path has finished (host-synchronised fallback)
+    const size_t chol = chol_workspace_bytes(off, nb);
+    A.sf = take(8ull * sq > chol ? 8ull * sq : chol);
     A.tf = take(8ull * (tfe > 0 ? tfe : 1));
     A.toff = take(8ull * nb);
     A.pdot = take(8ull * 2 * totch * QNB);
@@ -840,6 +843,16 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     upload_tab_kernel<<<1, 256, 0, st>>>(tab, const_cast<EBlk*>(B.tab));
     if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
     if (!a.mixed) return solve_fp64(B, tab, nmax, F, a, dtheta, evals, n_kept, np, status, st);
+
+    // ---- Gram-matrix blocks, eigenvalues not requested: certified Cholesky + refinement
+    if (a.psd && !(a.want_evals && evals) && chol_applicable(block_off, nb)) {
+        bool ok = false;
+        const size_t cb = chol_workspace_bytes(block_off, nb);
+        const int rc = launch_chol_solve(S, block_off, nb, F, a, dtheta, n_kept, W + LA.sf, cb, status, st, &ok);
+        if (rc) return rc;
+        if (ok) return NQS_OK;
+        // some block not certified, not factored or not converged: eigen-decomposition path
+    }
 
     // ---- mixed precision
     MixBufs M;

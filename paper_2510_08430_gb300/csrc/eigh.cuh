@@ -78,6 +78,16 @@ struct MixBufs {
     int* fallback;        // per slot: cutoff may drop an eigenvalue (needs the FP64 path)
 };
 
+// Cholesky path for Gram-matrix blocks (chol.cu): certificate from ||S_b||_F, FP32 tiled
+// Cholesky of S_b + lambda I, FP64-residual refinement. Blocks of at most 65536 parameters.
+bool chol_applicable(const int64_t* block_off, int nb);
+size_t chol_workspace_bytes(const int64_t* block_off, int nb);
+// Writes dtheta and n_kept when every block succeeds. *ok_out (host): every block certified,
+// factored and converged (always true under capture, where a failure is NQS_ERR_RETRY).
+int launch_chol_solve(const c128* S, const int64_t* block_off, int nb, const c128* F, const SolveArgs& a,
+                      c128* dtheta, int32_t* n_kept, void* work, size_t work_bytes, DevStatus* status,
+                      cudaStream_t st, bool* ok_out);
+
 // Persistent cooperative kernels (eigh_persist.cu). `bar` points to two zeroed words
 // of grid-barrier state; every grid-wide wait is bounded and reports NQS_ERR_TIMEOUT.
 template <typename R>

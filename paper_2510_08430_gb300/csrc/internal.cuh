@@ -73,7 +73,7 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 // nsplit 0: dO written in place (prec FP64/FP32); nsplit 2 or 3: element-wise BF16
 // split planes of dO (O is c128, unchanged)
 // (split modes also write diag[k] = sum_s w_s |dO_k(s)|^2 in FP64; nsplit 5 = grouped
-// error-free split with int8 exponents gexp[group][param], groups of 16 samples)
+// error-free split with int8 exponents gexp[group][param], groups of GRAM_GROUP samples)
 cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long ns, long long np, const c128* eloc,
                               c128* osum, c128* esum, cudaStream_t st);
 cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st);
@@ -110,6 +110,7 @@ struct GramTable {
 cudaError_t launch_gram_simt(int prec, const void* dO, long long ldo, long long ns, const double* w,
                              double scale, const GramTable& tab, c128* S, cudaStream_t st);
 constexpr int GRAM_KPI_DEFAULT = 4;    // MMA K-steps (16 samples) per accumulator flush
+constexpr int GRAM_GROUP = 64;         // samples per exponent group of the grouped split (gexp rows)
 // tcgen05 Gram over nsplit element-wise BF16 split planes (2: 3 products; 3: 6 products),
 // FP32 accumulation per 64-sample K block folded into double-float sums;
 // cudaErrorNotSupported off sm_103.

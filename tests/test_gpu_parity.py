@@ -221,6 +221,45 @@ def test_mixed_solver_matches_definition(sizes, solver):
         np.testing.assert_allclose(evg[off[b]:off[b + 1]], sig[b], rtol=0, atol=1e-5 * sig[b].max())
 
 
+@pytest.mark.parametrize("sizes", [[1, 2, 3], [17, 65, 130], [300, 64], [64, 129, 5], [700]])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cholesky_path_matches_definition(sizes, mode):
+    """Gram-matrix blocks without eigenvalue output take the certified Cholesky path (FP32
+    tiled factor, FP64 refinement): equal to the pseudo-inverse definition to 1e-10, in both
+    cutoff modes, on ragged tiles (1 .. 700 parameters, 64-wide tiles)."""
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rng = np.random.default_rng(19)
+    blocks = []
+    for n in sizes:
+        X = rng.normal(size=(n + 7, n)) + 1j * rng.normal(size=(n + 7, n))
+        X[:, : n // 3] *= 3e-2  # spread the spectrum
+        blocks.append(np.conj(X).T @ X / X.shape[0])
+    F = rng.normal(size=off[-1]) + 1j * rng.normal(size=off[-1])
+    S = torch.as_tensor(np.concatenate([B.ravel() for B in blocks]), device="cuda")
+    cut = 1e-10 if mode == 0 else 1e-6
+    dth, ev, nk = nq().qgt_block_solve(S, off, torch.as_tensor(F, device="cuda"), 1e-3, cut, mode, 0.8,
+                                       want_evals=False, solver="mixed_psd")
+    assert ev is None
+    ref, sig, kept = oracle.qgt.block_solve(blocks, F, off, 1e-3, cut, 0.8, absolute=mode == 1)
+    assert np.array_equal(nk.cpu().numpy(), kept) and np.array_equal(kept, np.array(sizes))
+    assert rel(dth.cpu().numpy(), ref) < 1e-10
+
+
+def test_cholesky_path_hands_a_binding_cutoff_to_the_eigen_path():
+    """When the certificate cannot show that the cutoff keeps everything, the solve must
+    still equal the definition (eigen-decomposition path), with the dropped count exact."""
+    sizes = [40, 9, 130]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    blocks = [_herm_psd(n, 3 + n, np.logspace(-6, 0, n)) for n in sizes]
+    F = np.random.default_rng(1).normal(size=off[-1]) + 0j
+    S = torch.as_tensor(np.concatenate([B.ravel() for B in blocks]), device="cuda")
+    dth, _, nk = nq().qgt_block_solve(S, off, torch.as_tensor(F, device="cuda"), 1e-8, 3e-3, 0, 1.0,
+                                      want_evals=False, solver="mixed_psd")
+    ref, _, kept = oracle.qgt.block_solve(blocks, F, off, 1e-8, 3e-3, 1.0)
+    assert np.array_equal(nk.cpu().numpy(), kept) and kept.min() < min(sizes)
+    assert rel(dth.cpu().numpy(), ref) < 1e-9
+
+
 def test_mixed_solver_falls_back_when_cutoff_binds():
     sizes = [40, 9]
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
