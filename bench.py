@@ -4,8 +4,9 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 A step is the whole hot path: Jacobian of ln psi, local energies, centring and
-force, the per-layer QGT blocks (tcgen05 BF16 hi+lo Gram) and the per-block
-FP64 shifted pseudo-inverse solve, from (theta, configs) to (dtheta, <E>).
+force, the per-layer QGT blocks (tcgen05 Gram on an error-free BF16 split) and the
+per-block shifted pseudo-inverse solve (certified FP32 Cholesky + FP64 refinement),
+from (theta, configs) to (dtheta, <E>).
 Default workload: FFNN 100-64-64-64-64-1 on the periodic 10x10 J1-J2 lattice
 (J2/J1 = 0.5), 16384 zero-magnetisation samples, blocks 6464/4160/4160/4160/65,
 seeded synthetic inputs. Prints one JSON line (rank 0).
@@ -14,7 +15,8 @@ Timing: W untimed warm-up steps; K timed steps bracketed by a barrier and
 device synchronisation, each step timed with CUDA events on the launching
 stream, L2 flushed (256 MB write) between steps; the maximum over ranks is
 reported. With N > 1 every rank runs its own independent replica of the
-workload (no data-path collective; weak scaling).
+workload (no data-path collective; weak scaling). With --sharded, one instance is
+split over the N ranks by samples (three exchanges over NCCL; strong scaling).
 """
 from __future__ import annotations
 
@@ -46,11 +48,14 @@ def parse():
     ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharded", action="store_true",
+                    help="split ONE instance over the ranks by samples (three exchanges over NCCL; strong scaling)")
     return ap.parse_args()
 
 
 SOLVER_DESC = {"fp64": "FP64 Householder eigensolver",
-               "mixed": "FP32 Householder reduction + FP64-residual refinement (PSD certificate, FP64 fallback)"}
+               "mixed": "certified FP32 tiled Cholesky + FP64-residual refinement (keep-all certificate from "
+                        "||S_b||_F; FP32 Householder + refinement, then FP64 eigensolver, as fallbacks)"}
 
 
 def workload_desc(w, solver="mixed") -> dict:
@@ -91,41 +96,57 @@ def gram_flops(w) -> tuple:
     return alg, full, issued
 
 
-def trd_bytes(w, solver: str) -> float:
-    """Algorithmic DRAM bytes of one launch of the (unblocked, fused) Householder reduction
-    of all blocks: for every column, the lower triangle (diagonal included) of the trailing
-    m x m matrix is read once (Hermitian matvec) and written once (rank-2 update),
-    m = n_b - 1 .. 1, i.e. 2 * esize * (n_b - 1) n_b (n_b + 1) / 6 bytes per block; esize is
-    8 (complex64, mixed solver) or 16 (complex128, FP64 solver)."""
+def chol_flops(w) -> float:
+    """Real flops of the complex Cholesky factorization of every block: n^3/6 complex
+    multiply-adds (8 real flops each) per block of n parameters."""
     import numpy as np
     nb = np.diff(w.block_off).astype(np.float64)
-    es = 8.0 if solver == "mixed" else 16.0
-    return float(np.sum(2.0 * es * (nb - 1.0) * nb * (nb + 1.0) / 6.0))
+    return float(np.sum(8.0 * nb ** 3 / 6.0))
 
 
-def trd_traffic(w, solver: str):
-    """DRAM bytes per launch of the reduction kernel from the committed ncu summary, or None
-    when the summary is missing, is for another workload/solver, or the kernel source has
-    changed since it was taken (sha256 of eigh_persist.cu recorded in the summary)."""
-    import hashlib
+def fp32_peak_tflops(sm_mhz) -> float:
+    """FP32 FMA peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA
+    x the SM clock (the clock sampled under load during the timed region, else the maximum
+    2070 MHz)."""
+    mhz = sm_mhz if sm_mhz else 2070.0
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def eloc_roofline(w, ms: float, fp32_peak: float) -> dict:
+    """Local energies against the FP32 pipe. Unit of work: one connected configuration (an
+    anti-aligned bond of a sample) pushed through hidden layers 2..L-1 and the output
+    layer, in_l x out_l complex multiply-adds each (8 real flops), counted as FP64 flops;
+    the kernel evaluates them in double-float (FP32 pairs), about 11 FP32 operations per
+    FP64-equivalent flop, so the bound is fp32_peak / 11."""
     import numpy as np
-    path = os.path.join(ROOT, "profiles", f"trd_persist_{w.name}.md")
-    src = os.path.join(ROOT, "paper_2510_08430_gb300", "csrc", "eigh_persist.cu")
-    if not os.path.exists(path) or not os.path.exists(src):
-        return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    rec = {}
-    for line in open(path):
-        if line.startswith("- ") and ": " in line:
-            k, v = line[2:].split(": ", 1)
-            rec[k.strip()] = v.strip().strip("`")
-    blocks = ",".join(str(int(v)) for v in np.diff(w.block_off))
-    if rec.get("source_sha256") != sha or rec.get("solver") != solver or rec.get("blocks") != blocks:
-        return None  # the reduction's traffic depends on the blocks only, not on N_s
-    try:
-        return float(rec["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    x = w.configs.astype(np.int64)
+    ij = np.asarray(w.bond_ij)
+    n_conn = int(np.sum(x[:, ij[:, 0]] != x[:, ij[:, 1]]))
+    widths = list(w.model.widths)
+    per = sum(8.0 * widths[l] * widths[l + 1] for l in range(1, len(widths) - 1))
+    flops = n_conn * per
+    peak = fp32_peak / 11.0
+    ach = flops / (ms / 1e3) / 1e12
+    return {"kernel": "conn_terms_df_kernel (connected forwards, double-float hidden layers)", "bound": "alu",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "peak_source": "derived: FP32 FMA peak (152 x 128 x 2 x SM clock) / 11 FP32 ops per double-float flop",
+            "algorithmic": "connections x sum_{l>=1} 8 in_l out_l (FP64-equivalent flops)",
+            "connections": n_conn, "algorithmic_flops": flops, "ms_per_step": ms, "traffic": None}
+
+
+def dtheta_accuracy(w, dth) -> dict:
+    """Relative l2 error of the timed step's dtheta against the stored FP64 oracle result of
+    this workload (tests/golden, written by a script that calls only the oracle)."""
+    import numpy as np
+    gold = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.npz")
+    bar = {"fp64": 1e-10, "fp32": 1e-4}.get(w.precision, 1e-6)
+    if not os.path.exists(gold) or w.n_samples != W_DEFAULT_NS.get(w.name):
+        return {"dtheta_rel_err_vs_oracle": None, "bar": bar, "within": False,
+                "note": "no stored oracle result for this workload size"}
+    ref = np.load(gold)["dtheta"]
+    err = float(np.linalg.norm(dth - ref) / np.linalg.norm(ref))
+    return {"dtheta_rel_err_vs_oracle": err, "bar": bar, "within": bool(err <= bar),
+            "reference": f"tests/golden/oracle_{w.name}.npz (FP64 oracle)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -175,39 +196,64 @@ class Clocks:
 def oracle_sample(w, n_sample: int = 1024, eig_n: int = 2048) -> dict:
     """Time the FP64 oracle on a bounded sample of the workload and extrapolate one step.
 
-    Stages linear in N_s (Jacobian, E_loc, centring, force, block Gram) run on
-    the first n_sample samples and scale by N_s / n_sample; the per-block eigh +
-    pseudo-inverse runs on one eig_n x eig_n Hermitian block and scales by
-    sum_b n_b^3 / eig_n^3.
+    Stages linear in N_s (Jacobian, E_loc, centring + force, block Gram) run on the first
+    n_sample samples and scale by N_s / n_sample; the per-block eigh + pseudo-inverse runs
+    on one eig_n x eig_n Hermitian block and scales by sum_b n_b^3 / eig_n^3.
     """
     import numpy as np
     import oracle
     import workloads as W
     ws = W.make_workload(w.name, n_sample)
+    t = {}
     t0 = time.perf_counter()
     lp, O = oracle.nqs.jacobian(ws.model, ws.theta, ws.configs)
+    t["jacobian"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     el = oracle.hamiltonian.local_energy(ws.model, ws.theta, ws.configs, ws.bond_ij, ws.bond_j, ws.c, ws.sign_rule)
+    t["local_energy"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     _, _, dO, e = oracle.qgt.center(O, el)
     F = oracle.qgt.force(dO, e)
-    S = oracle.qgt.block_qgt(dO, ws.block_off)
-    t_lin = time.perf_counter() - t0
+    t["centring_force"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.qgt.block_qgt(dO, ws.block_off)
+    t["gram"] = time.perf_counter() - t0
     rng = np.random.default_rng(0)
     X = rng.normal(size=(eig_n, eig_n)) + 1j * rng.normal(size=(eig_n, eig_n))
     Sb = X @ np.conj(X).T / eig_n
-    t1 = time.perf_counter()
+    t0 = time.perf_counter()
     oracle.qgt.pinv_solve(Sb, F[:eig_n] if F.shape[0] >= eig_n else np.ones(eig_n, complex), w.diag_shift,
                           w.cutoff)
-    t_eig = time.perf_counter() - t1
+    t_eig = time.perf_counter() - t0
     nb = np.diff(w.block_off).astype(np.float64)
-    est = t_lin * w.n_samples / n_sample + t_eig * float(np.sum(nb ** 3)) / eig_n ** 3
+    lin_scale = w.n_samples / n_sample
+    eig_scale = float(np.sum(nb ** 3)) / eig_n ** 3
+    stages = {k: v * lin_scale for k, v in t.items()}
+    stages["eigh_solve"] = t_eig * eig_scale
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
         cores = os.cpu_count()
-    return {"seconds_per_step": est, "measured_seconds": t_lin + t_eig, "cores": cores,
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", cores)))
+    return {"seconds_per_step": float(sum(stages.values())), "stage_seconds": stages,
+            "measured_seconds": float(sum(t.values()) + t_eig), "cores": cores, "threads": threads,
             "sample": (f"oracle on {n_sample} of {w.n_samples} samples (Jacobian, E_loc, centring, force, "
-                       f"block Gram; scaled x{w.n_samples / n_sample:g}) plus one {eig_n}x{eig_n} eigh+pinv "
-                       f"(scaled by sum n_b^3/{eig_n}^3); NumPy/LAPACK threads = all cores")}
+                       f"block Gram; scaled x{lin_scale:g}) plus one {eig_n}x{eig_n} eigh+pinv "
+                       f"(scaled by sum n_b^3/{eig_n}^3 = {eig_scale:.3g}); NumPy/LAPACK threads = {threads}")}
+
+
+def oracle_sample_single_thread(w, n_sample: int = 256, eig_n: int = 1024) -> dict:
+    """The same bounded oracle sample on one host thread, in a child process whose BLAS
+    thread count is fixed before NumPy loads."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, workloads as W; "
+            "w = W.make_workload(%r, %d); print(json.dumps(bench.oracle_sample(w, %d, %d)))"
+            % (ROOT, w.name, w.n_samples, n_sample, eig_n))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # report, do not fail the bench line
+        return {"unavailable": str(exc)[:200]}
 
 
 # ------------------------------------------------------------------ measured peaks
@@ -298,11 +344,12 @@ def run_reference(args, rank: int, world: int) -> None:
     w = W.make_workload(args.workload, args.samples)
     for _ in range(args.warmup):
         oracle_sample(w)
-    secs = []
+    secs, measured = [], []
     info = None
     for _ in range(args.steps):
         info = oracle_sample(w)
         secs.append(info["seconds_per_step"])
+        measured.append(info["measured_seconds"])
     t = sum(secs)
     value = args.steps / t
     line = {
@@ -311,8 +358,11 @@ def run_reference(args, rank: int, world: int) -> None:
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_desc(w, "mixed"),
         "reference_impl": "FP64 NumPy oracle (same workload and metric; FP64 Jacobian, E_loc, Gram and LAPACK eigh)",
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": info["cores"], "kind": "oracle",
-                         "sample": info["sample"]},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": info["cores"], "threads": info["threads"],
+                         "kind": "oracle", "sample": info["sample"], "stage_seconds": info["stage_seconds"]},
+        "sample_seconds_per_step": sum(measured) / args.steps,
+        "note": "each step times a bounded oracle sample and scales it to the full workload; ms_per_step is "
+                "that extrapolated full step, sample_seconds_per_step what one sample took",
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -409,37 +459,54 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     st_mean = {k: statistics.mean(d[k] for d in stages) for k in stages[0]}
     alg, full, issued = gram_flops(w)
     gram_s = st_mean["gram"] / 1e3
-    trd_s = st_mean["tridiagonal_reduction"] / 1e3
-    hbm = peaks["hbm_gbs"]
-    trd_alg = trd_bytes(w, args.solver)
-    trd_gbs = trd_alg / trd_s / 1e9
-    traffic = trd_traffic(w, args.solver)
     bf16_peak = peaks["bf16_tflops"]
     gram_tf = alg / gram_s / 1e12
+    gram_kernel = ("gram_tc_kernel<5,true,32> (tcgen05, grouped error-free split)" if w.precision == "split_bf16_exact"
+                   else "gram_tc_kernel (tcgen05, element-wise split)" if w.precision.startswith("split")
+                   else f"gram_simt_kernel ({w.precision} FMA)")
+    roof_gram = {"kernel": gram_kernel, "bound": "tensor" if w.precision.startswith("split") else "alu",
+                 "achieved": gram_tf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": gram_tf / bf16_peak,
+                 "peak_source": f"bf16_tflops burst, {peaks['source']}",
+                 "frac_of_sustained": gram_tf / peaks["bf16_tflops_sustained"],
+                 "issued_tflops": issued / gram_s / 1e12, "issued_frac": issued / gram_s / 1e12 / bf16_peak,
+                 "algorithmic": "sum_b 4 n_b (n_b+1) N_s flops (unique lower triangle)",
+                 "algorithmic_flops": alg, "full_count_tflops": full / gram_s / 1e12,
+                 "ms_per_launch": st_mean["gram"], "traffic": None}
+    fp32_peak = fp32_peak_tflops(clk.get("sm_mhz"))
+    fac_s = st_mean["factorization"] / 1e3
+    roof_fac = {"kernel": "chol_potrf/trsm/herk_kernel (FP32 tiled Cholesky of every block, one launch per panel)",
+                "bound": "alu", "achieved": chol_flops(w) / fac_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": chol_flops(w) / fac_s / 1e12 / fp32_peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x median SM clock under load",
+                "algorithmic": "sum_b 8 n_b^3 / 6 real flops (complex Cholesky)", "algorithmic_flops": chol_flops(w),
+                "ms_per_step": st_mean["factorization"], "traffic": None}
+    # the roofline line is the stage that takes the most time
+    dominant = max(("gram", "factorization", "local_energy"), key=lambda k: st_mean[k])
+    if dominant == "gram":
+        roof = roof_gram
+    elif dominant == "factorization":
+        roof = roof_fac
+    else:
+        roof = eloc_roofline(w, st_mean["local_energy"], fp32_peak)
+    # accuracy of the timed step against the stored FP64 oracle result (the metric's bar)
+    acc = dtheta_accuracy(w, dth_split)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
         "config": dict(workload_desc(w, args.solver), parallelism=("replicas" if world > 1 else "single")),
         "stage_ms": st_mean,
-        "roofline": {"kernel": ("trd_persist_kernel<float>" if args.solver == "mixed" else
-                                "trd_persist_kernel<double>") + " (Householder reduction of all blocks, one launch)",
-                     "bound": "hbm", "achieved": trd_gbs, "peak": hbm, "unit": "GB/s", "frac": trd_gbs / hbm,
-                     "traffic": traffic,
-                     "peak_source": f"hbm_gbs, {peaks['source']}",
-                     "algorithmic": "per block 2 * esize * (n_b-1) n_b (n_b+1) / 6 bytes (trailing lower triangle "
-                                    "read + written once per column)",
-                     "algorithmic_bytes": trd_alg, "ms_per_launch": st_mean["tridiagonal_reduction"]},
-        "roofline_gram": {"kernel": f"gram_tc_kernel (tcgen05, {w.precision})", "bound": "tensor",
-                          "achieved": gram_tf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": gram_tf / bf16_peak,
-                          "peak_source": f"bf16_tflops burst, {peaks['source']}",
-                          "issued_tflops": issued / gram_s / 1e12,
-                          "algorithmic": "sum_b 4 n_b (n_b+1) N_s flops (unique lower triangle)",
-                          "full_count_tflops": full / gram_s / 1e12},
+        "dtheta_within_tol": acc["within"],
+        "accuracy": acc,
+        "roofline": dict(roof, dominant_stage=dominant),
+        "roofline_gram": roof_gram,
+        "roofline_factorization": roof_fac,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
     }
+    if not acc["within"]:
+        line["invalid"] = "dtheta misses the metric's 1e-6 bar against the FP64 oracle (or was not checked)"
     # the same step captured as one CUDA graph and replayed (launch overhead removed)
     try:
         step.capture(theta, x)
@@ -465,8 +532,96 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         line["comparisons"] = compare_steps(nq, torch, np, w, model, ham, theta, x, dth_split, args.solver)
     if world == 1 and not args.no_cpu_baseline:
         info = oracle_sample(w)
+        one = oracle_sample_single_thread(w)
         line["cpu_baseline"] = {"value": 1.0 / info["seconds_per_step"], "unit": "steps/s", "cores": info["cores"],
-                                "kind": "oracle", "sample": info["sample"]}
+                                "threads": info["threads"], "kind": "oracle", "sample": info["sample"],
+                                "stage_seconds": info["stage_seconds"],
+                                "measured_seconds": info["measured_seconds"],
+                                "single_thread": ({"value": 1.0 / one["seconds_per_step"], "unit": "steps/s",
+                                                   "threads": 1, "sample": one["sample"],
+                                                   "stage_seconds": one["stage_seconds"]}
+                                                  if "seconds_per_step" in one else one)}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ sample-sharded arm
+class _LocalComm:
+    """The sharded step's collectives for a single rank (nothing to exchange)."""
+
+    def all_reduce(self, t):
+        pass
+
+    def reduce(self, t, dst):
+        pass
+
+    def all_gather(self, out, t):
+        out[0].copy_(t)
+
+
+def run_sharded(args, rank: int, world: int, local_rank: int) -> None:
+    """One instance of the workload, its samples split over the ranks: every rank runs the
+    Jacobian, local energies and its shard's part of S and F; the shard sums are all-reduced,
+    S and F reduced to their block owners, and the owners' dtheta slices all-gathered
+    (paper_2510_08430_gb300.sharded.step_distributed). value = instance steps per second."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_08430_gb300 as nq
+    from paper_2510_08430_gb300 import sharded
+    import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    w = W.make_workload(args.workload, args.samples)
+    model = nq.Model.from_workload(w.model)
+    ham = nq.Hamiltonian(w.model.n_sites, w.bond_ij, w.bond_j, w.c, w.sign_rule)
+    idx = np.array_split(np.arange(w.n_samples), world)[rank]
+    theta = torch.as_tensor(w.theta, device="cuda")
+    x = torch.as_tensor(w.configs[idx], device="cuda")
+    be = sharded.LibraryShardBackend(model, ham, w.block_off, w.precision, args.solver)
+    comm = sharded.TorchComm() if world > 1 else _LocalComm()
+
+    def step():
+        return sharded.step_distributed(be, theta, x, w.n_samples, w.block_off, w.diag_shift, w.cutoff,
+                                        comm=comm, rank=rank, world=world)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local_rank)
+    l0 = nq.launch_count()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        dth, em = step()
+    e.record()
+    barrier()
+    clk = clocks.stop()
+    launches = nq.launch_count() - l0
+    total = torch.tensor([s.elapsed_time(e) / 1e3], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    t_max = float(total.item())
+    acc = dtheta_accuracy(w, dth.cpu().numpy())
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": args.steps / t_max, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
+        "config": dict(workload_desc(w, args.solver), parallelism=f"samples sharded over {world} ranks",
+                       exchanges="all-reduce of shard sums (n_p + 1 complex); reduce of S_b, F_b to block owners; "
+                                 "all-gather of owners' dtheta"),
+        "dtheta_within_tol": acc["within"], "accuracy": acc, "clocks": clk, "gpu_launches": int(launches),
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -483,7 +638,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.sharded:
+        run_sharded(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -279,11 +279,12 @@ NQS_API int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p
  *                  at 1/64 of the FP32 rate on GB300); Q is formed explicitly in FP32;
  *                  eigenvalues come from the FP32-reduced tridiagonal; dtheta_b is then
  *                  obtained by iterative refinement whose residuals F - (S_b + lambda I) x
- *                  use the FP64 S_b, until ||r|| <= 1e-14 ||F_b|| (NQS_ERR_NOT_CONVERGED
- *                  after 30 sweeps). When the FP32 eigenvalues cannot certify that the
- *                  cutoff keeps every eigenvalue of a block (margin 4e-5 sigma_max), every
- *                  block is solved by the FP64 path instead; deciding this synchronises
- *                  the stream once. S_packed is left unchanged in the refinement case.
+ *                  use the FP64 S_b, until ||r|| <= 1e-14 ||F_b||. When the FP32
+ *                  eigenvalues cannot certify that the cutoff keeps every eigenvalue of a
+ *                  block (margin 4e-5 sigma_max), or a block's refinement has not converged
+ *                  after 30 sweeps, every block is solved by the FP64 path instead; each
+ *                  decision synchronises the stream once (under NQS_GRAPH either is recorded
+ *                  as NQS_ERR_RETRY). S_packed is left unchanged in the refinement case.
  * NQS_SOLVE_MIXED_PSD: as NQS_SOLVE_MIXED, with the caller asserting that every S_b is
  *                  a Gram matrix (positive semi-definite up to a rounding of at most
  *                  1e-6 sigma_max, as qgt_block_build produces), so sigma_min >= shift -

@@ -256,12 +256,12 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 }
 
 // Grouped error-free split (O is c128, unchanged): for every parameter row and every
-// group of GROUP = 64 samples, E = exponent of the group's max |Re|, |Im| of sqrt(w) dO;
+// group of GROUP = 32 samples, E = exponent of the group's max |Re|, |Im| of sqrt(w) dO;
 // each value t = x 2^-E (|t| < 1) is rounded once to N = rint(t 2^39) and N is written in
 // balanced base 256, N = sum_q d_q 2^(8(4-q)) with |d_q| <= 128; slice q is the BF16
 // value d_q 2^-(8q+7) (an integer of at most 8 bits times a power of two, exact in
-// BF16). Products of slices of one group then lie on a common grid: a sum of 64 leading
-// products is below 2^20 grid units and exact in FP32, so the tensor-core Gram accumulates
+// BF16). Products of slices of one group then lie on a common grid: a sum of 32 leading
+// products is below 2^19 grid units and exact in FP32, so the tensor-core Gram accumulates
 // a whole group in tensor memory before its epilogue scales it by 2^(E_k + E_l).
 
 // Balanced base-256 digits of |N| < 2^39, most significant first.
@@ -274,8 +274,8 @@ __device__ __forceinline__ void digits5(long long N, int (&d)[5]) {
     }
     d[0] = (int)N;
 }
-constexpr int GROUP = GRAM_GROUP;  // samples per exponent group: one warp, two samples per lane
-static_assert(GROUP == 64, "one warp of two samples per lane");
+constexpr int GROUP = GRAM_GROUP;  // samples per exponent group: one warp, one sample per lane
+static_assert(GROUP == 32, "one warp per exponent group");
 __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restrict__ O, long long ldo, long long ns,
                                                             const double* __restrict__ w,
                                                             const c128* __restrict__ e, c128* __restrict__ F,
@@ -310,57 +310,42 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
     }
     double fr = 0.0, fi = 0.0, dg = 0.0;
     __nv_bfloat16* pls[5] = {pl0, pl1, pl2, pl3, pl4};
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    // warp wid takes groups wid, wid + nwarp, ...; each lane holds samples s0 and s0 + 1
-    for (long long g = wid; g * GROUP < ldk; g += nwarp) {
-        const long long s0 = g * GROUP + 2 * lane;
-        double dr[2], di[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long long s = s0 + h;
-            dr[h] = 0.0;
-            di[h] = 0.0;
-            if (s < ns) {
-                const c128 v = row[s];
-                const double ws = w ? w[s] : uw;
-                dr[h] = v.re - mr;
-                di[h] = v.im - mi;
-                const c128 es = e[s];
-                fr = fma(ws, fma(dr[h], es.re, di[h] * es.im), fr);
-                fi = fma(ws, fma(dr[h], es.im, -di[h] * es.re), fi);
-                dg = fma(ws, fma(dr[h], dr[h], di[h] * di[h]), dg);
-                if (w) {
-                    const double sw = sqrt(ws);
-                    dr[h] *= sw;
-                    di[h] *= sw;
-                }
+    const int lane = threadIdx.x & 31;
+    // blockDim.x is a multiple of 32 and ldk of GROUP: the samples of a group are one warp
+    for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
+        double dr = 0.0, di = 0.0;
+        if (s < ns) {
+            const c128 v = row[s];
+            const double ws = w ? w[s] : uw;
+            dr = v.re - mr;
+            di = v.im - mi;
+            const c128 es = e[s];
+            fr = fma(ws, fma(dr, es.re, di * es.im), fr);
+            fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
+            dg = fma(ws, fma(dr, dr, di * di), dg);
+            if (w) {
+                const double sw = sqrt(ws);
+                dr *= sw;
+                di *= sw;
             }
         }
-        double mx = fmax(fmax(fabs(dr[0]), fabs(di[0])), fmax(fabs(dr[1]), fabs(di[1])));
+        double mx = fmax(fabs(dr), fabs(di));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         // E with mx = m 2^E, m in [0.5, 1) (frexp convention), from the exponent bits
         int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
         ex = mx > 0.0 ? ex : 0;
         ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
-        if (lane == 0) gexp[g * gstride + p] = (int8_t)ex;
+        if (lane == 0) gexp[(s / GROUP) * gstride + p] = (int8_t)ex;
         const double sc = __longlong_as_double((long long)(1023 + 39 - ex) << 52);  // 2^(39 - E)
-        int dr5[2][5], di5[2][5];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            digits5(__double2ll_rn(dr[h] * sc), dr5[h]);
-            digits5(__double2ll_rn(di[h] * sc), di5[h]);
-        }
+        int dr5[5], di5[5];
+        digits5(__double2ll_rn(dr * sc), dr5);
+        digits5(__double2ll_rn(di * sc), di5);
         const float qs[5] = {0x1p-7f, 0x1p-15f, 0x1p-23f, 0x1p-31f, 0x1p-39f};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            __nv_bfloat162 re2, im2;
-            re2.x = __float2bfloat16_rn((float)dr5[0][q] * qs[q]);
-            re2.y = __float2bfloat16_rn((float)dr5[1][q] * qs[q]);
-            im2.x = __float2bfloat16_rn((float)di5[0][q] * qs[q]);
-            im2.y = __float2bfloat16_rn((float)di5[1][q] * qs[q]);
-            *reinterpret_cast<__nv_bfloat162*>(pls[q] + (2 * p) * ldk + s0) = re2;
-            *reinterpret_cast<__nv_bfloat162*>(pls[q] + (2 * p + 1) * ldk + s0) = im2;
+            pls[q][(2 * p) * ldk + s] = __float2bfloat16_rn((float)dr5[q] * qs[q]);
+            pls[q][(2 * p + 1) * ldk + s] = __float2bfloat16_rn((float)di5[q] * qs[q]);
         }
     }
     fr = block_sum(fr, sh);

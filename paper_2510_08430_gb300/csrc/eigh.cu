@@ -570,6 +570,12 @@ __global__ void __launch_bounds__(256) mix_cert_kernel(SolveBufs B, MixBufs M, i
     }
 }
 
+__global__ void not_done_status_kernel(const int* __restrict__ done, int nb, DevStatus* status) {
+    int any = 0;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) any |= !done[j];
+    if (__any_sync(0xffffffffu, any) && threadIdx.x == 0) set_status(status, NQS_ERR_RETRY, W_SOLVE, -2);
+}
+
 __global__ void retry_status_kernel(const int* __restrict__ fallback, int nb, DevStatus* status) {
     int any = 0;
     for (int j = threadIdx.x; j < nb; j += blockDim.x) any |= fallback[j];
@@ -937,7 +943,20 @@ int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
     if (rc) return rc;
     count_launch();
     ref_out_kernel<<<nb, 256, 0, st>>>(B, M, a.eta, dtheta, n_kept);
-    return cudaGetLastError() == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
+    // a block whose refinement did not converge: the FP64 path for every block
+    if (a.no_host_sync) {
+        count_launch();
+        not_done_status_kernel<<<1, 32, 0, st>>>(M.done, nb, status);
+        return cudaGetLastError() == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
+    }
+    int dn[MAXB];
+    if (cudaMemcpyAsync(dn, M.done, sizeof(int) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return NQS_ERR_CUDA;
+    for (int j = 0; j < nb; ++j)
+        if (!dn[j]) return solve_fp64(B, tab, nmax, F, a, dtheta, evals, n_kept, np, status, st);
+    return NQS_OK;
 }
 
 }  // namespace nqs

@@ -6,7 +6,7 @@
 // Every entry is split into BF16 terms x = x1 + x2 (+ x3 (+ x4)) and G is accumulated
 // from the leading products x1 y1 (accumulator A0) and the correction products
 // (accumulator A1). Two splits: element-wise (each term the BF16 rounding of the
-// remainder, 2 or 3 terms), and grouped error-free (per parameter and 64-sample group
+// remainder, 2 or 3 terms), and grouped error-free (per parameter and 32-sample group
 // a common power of two, five slices of at most 8-bit integers; Ozaki, Ogita, Oishi
 // and Rump 2012), in which the A0 sums and the order-1 sums are exact. FP32 accumulation in tensor memory
 // spans at most one K block; the epilogue folds every work item into double-float
@@ -217,13 +217,12 @@ struct Maps {
     CUtensorMap m[5];
 };
 
-// Work item = (tile, kpi MMA K-steps of 16 samples; kpi is 1, 2 or 4). Each work item
+// Work item = (tile, kpi MMA K-steps of 16 samples; kpi divides KB / 16). Each work item
 // owns one of two accumulator pairs (A0, A1) in tensor memory; smem stages hold
 // one 64-sample K block each.
-// KB: samples per K block (64 or 32). GROUPED: every group of GRAM_GROUP samples carries its
-// own per-parameter exponents gexp[group][param]; the epilogue scales each group by
-// 2^(E_k + E_l) (one work item per group, kpi = GRAM_GROUP / 16 MMA K-steps, spanning
-// GRAM_GROUP / KB smem stages).
+// KB: samples per K block (64 or 32). GROUPED: every group of GRAM_GROUP = KB samples carries
+// its own per-parameter exponents gexp[group][param]; the epilogue scales each group by
+// 2^(E_k + E_l) (one work item per group and smem stage, kpi = KB / 16 MMA K-steps).
 template <int NSPLIT, bool GROUPED, int KB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_tc_kernel(const __grid_constant__ Maps maps, const __grid_constant__ GramTable tab, int nkb, int kpi,
@@ -311,14 +310,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_128x128();
-            // a work item spans kpi K-steps of 16 samples, possibly over several smem stages
-            // (kpi divides nkb * KSTEPS)
+            const int nsub = KSTEPS / kpi;
             uint32_t q = 0, w = 0;  // smem stage counter, accumulator work-item counter
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const TileInfo ti = decode(tab, t);
                 const bool diag = ti.I == ti.J;
-                int ks = 0;  // K-step within the tile
                 for (int kb = 0; kb < nkb && ok; ++kb, ++q) {
                     const int s = q % STAGES;
                     const uint32_t ph = (q / STAGES) & 1u;
@@ -326,27 +323,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     fence_after();
                     const uint32_t base = smem_u32(ring + (size_t)s * STAGE_BYTES);
                     const uint32_t boff = diag ? 0u : (uint32_t)(NS * KTILE_BYTES);
-                    for (int kk = 0; kk < KSTEPS; ++kk, ++ks) {
+                    for (int sub = 0; sub < nsub; ++sub, ++w) {
                         const uint32_t acc = w & 1u;
                         const uint32_t tmem_d = tmem_base + acc * BUF_COLS;
-                        const bool start = ks % kpi == 0;
-                        if (start) {
-                            if (!mbar_wait(&tempty_bar[acc], ((w >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
-                            fence_after();
-                        }
-                        const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes inside the swizzle row
+                        if (!mbar_wait(&tempty_bar[acc], ((w >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+                        fence_after();
+                        // product-major over the item's K-steps: every small product enters A1
+                        // before the large order-1 ones (Split<5> lists them last)
 #pragma unroll
                         for (int pr = 0; pr < SP::NPROD; ++pr) {
-                            const uint32_t aad = base + SP::pa(pr) * KTILE_BYTES + off;
-                            const uint32_t bad = base + boff + SP::pb(pr) * KTILE_BYTES + off;
-                            // product 0 -> A0; products 1.. -> A1; the first write of each resets it
-                            const uint32_t first = (start && pr <= 1) ? 0u : 1u;
-                            umma(tmem_d + (pr == 0 ? 0u : 128u), sdesc<KB>(aad), sdesc<KB>(bad), idesc, first);
+                            for (int kk = sub * kpi; kk < (sub + 1) * kpi; ++kk) {
+                                const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes inside the swizzle row
+                                const uint32_t aad = base + SP::pa(pr) * KTILE_BYTES + off;
+                                const uint32_t bad = base + boff + SP::pb(pr) * KTILE_BYTES + off;
+                                // product 0 -> A0; products 1.. -> A1; the first write of each resets it
+                                const uint32_t first = (kk == sub * kpi && pr <= 1) ? 0u : 1u;
+                                umma(tmem_d + (pr == 0 ? 0u : 128u), sdesc<KB>(aad), sdesc<KB>(bad), idesc, first);
+                            }
                         }
-                        if (ks % kpi == kpi - 1) {
-                            umma_commit(&tfull_bar[acc]);   // hands the accumulator pair to the epilogue
-                            ++w;
-                        }
+                        umma_commit(&tfull_bar[acc]);   // hands the accumulator pair to the epilogue
                     }
                     if (!ok) break;
                     umma_commit(&empty_bar[s]);     // frees the smem stage when these MMAs complete
@@ -368,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int cpar = r & 1;             // 0: Re row, 1: Im row of complex row r/2
         uint32_t q = 0;
         bool ok = true;
-        const int nitems = nkb * KSTEPS / kpi;
+        const int nitems = nkb * (KSTEPS / kpi);
         for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const TileInfo ti = decode(tab, t);
             const GBlk blk = tab.b[ti.b];
@@ -562,7 +557,8 @@ cudaError_t launch_gram_tc(int nsplit, const void* const* planes, const int8_t* 
     }
     if (nsplit == 2) return launch_tc<2, false, 64>(maps, tab, kpad, kpi, scale, nullptr, np, S, status, sms, st);
     if (nsplit == 3) return launch_tc<3, false, 64>(maps, tab, kpad, kpi, scale, nullptr, np, S, status, sms, st);
-    // one work item per exponent group: GRAM_GROUP samples = GRAM_GROUP / 16 MMA K-steps
+    // one work item per exponent group = one 32-sample K block (two MMA K-steps)
+    static_assert(GRAM_GROUP == 32, "an exponent group is one smem stage of the grouped kernel");
     return launch_tc<5, true, 32>(maps, tab, kpad, GRAM_GROUP / 16, scale, gexp, np, S, status, sms, st);
 }
 

@@ -110,7 +110,7 @@ struct GramTable {
 cudaError_t launch_gram_simt(int prec, const void* dO, long long ldo, long long ns, const double* w,
                              double scale, const GramTable& tab, c128* S, cudaStream_t st);
 constexpr int GRAM_KPI_DEFAULT = 4;    // MMA K-steps (16 samples) per accumulator flush
-constexpr int GRAM_GROUP = 64;         // samples per exponent group of the grouped split (gexp rows)
+constexpr int GRAM_GROUP = 32;         // samples per exponent group of the grouped split (gexp rows)
 // tcgen05 Gram over nsplit element-wise BF16 split planes (2: 3 products; 3: 6 products),
 // FP32 accumulation per 64-sample K block folded into double-float sums;
 // cudaErrorNotSupported off sm_103.

@@ -125,17 +125,38 @@ def test_ql_sweep_limit_is_not_converged():
 
 
 @pytest.mark.parametrize("want_evals", [True, False])
-def test_refinement_sweep_limit_is_not_converged(want_evals):
-    """One refinement sweep of the mixed solvers cannot reach ||r|| <= 1e-14 ||F||."""
+def test_refinement_sweep_limit_hands_over_to_fp64(want_evals):
+    """One refinement sweep of the mixed solvers cannot reach ||r|| <= 1e-14 ||F||: the
+    unconverged blocks are handed to the FP64 path, whose result is still the definition."""
     import paper_2510_08430_gb300 as nq
-    from paper_2510_08430_gb300._lib import NQS_ERR_NOT_CONVERGED
     blocks, off, F = _psd_blocks([300, 129], 8)
+    ref, _, _ = oracle.qgt.block_solve(blocks, F, off, 1e-4, 1e-10)
     nq.api.set_limits(1, 0)
-    assert _code(_solve, blocks, off, F, 1e-4, 1e-10, "mixed_psd", want_evals) == NQS_ERR_NOT_CONVERGED
+    dth, _, _ = _solve(blocks, off, F, 1e-4, 1e-10, "mixed_psd", want_evals)
+    assert rel(dth.cpu().numpy(), ref) < 1e-10
     nq.api.set_limits(0, 0)
     dth, _, _ = _solve(blocks, off, F, 1e-4, 1e-10, "mixed_psd", want_evals)
-    ref, _, _ = oracle.qgt.block_solve(blocks, F, off, 1e-4, 1e-10)
     assert rel(dth.cpu().numpy(), ref) < 1e-10
+
+
+def test_refinement_sweep_limit_under_capture_is_retry():
+    """Under stream capture nothing can fall back on the host: an unconverged refinement is
+    recorded as NQS_ERR_RETRY for the caller to retake the step uncaptured."""
+    import paper_2510_08430_gb300 as nq
+    from paper_2510_08430_gb300._lib import NQS_ERR_RETRY, NQSError
+    w = W.make_workload("j1j2_6x6_ffnn", 128)
+    model, theta, x, ham = dev_inputs(w)
+    st = nq.SRStep(model, 128, ham, w.block_off, "split_bf16_exact", w.diag_shift, w.cutoff, solver="mixed")
+    st.capture(theta, x)
+    nq.api.set_limits(1, 0)
+    g = st.capture(theta, x)  # recaptured: the lowered limit is a kernel argument of the graph
+    st.replay()
+    with pytest.raises(NQSError) as ei:
+        st.ws.sync_status()
+    assert ei.value.code == NQS_ERR_RETRY
+    nq.api.set_limits(0, 0)
+    del g
+    _ok_step()
 
 
 @pytest.mark.parametrize("solver,want_evals", [("fp64", True), ("mixed_psd", False)])
