@@ -327,6 +327,7 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
  *   dtheta_out: c128 [n_p]; Emean_out: c128 [1].
  *   evals_out / n_kept_out as in qgt_block_solve (may be NULL).
  *   flags: NQS_SYNC makes the call synchronise and return device status.
+ *          NQS_PARAM_SPACE solves every block in parameter space (see below).
  *          NQS_GRAPH makes the call capturable into a CUDA graph (stream capture):
  *          nothing synchronises with the host. The mixed solver's certificate is then
  *          checked on the device; when it fails the step's dtheta is not the definition's
@@ -336,6 +337,21 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
  *          attributes and loads kernels). */
 #define NQS_SYNC 1
 #define NQS_GRAPH 2
+#define NQS_PARAM_SPACE 4
+/* Blocks wider than the sample count. With the mixed solver, diag_shift > 0, precision
+ * NQS_FP64 or NQS_SPLIT_BF16_EXACT and no NQS_PARAM_SPACE flag, a block with n_b > n_s is
+ * solved in sample space (push-through identity):
+ *   dtheta_b = -eta X_b^H pinv(X_b X_b^H + diag_shift I) eps,  X_b = dO_b / sqrt(n_s), eps = e / sqrt(n_s),
+ * with an n_s x n_s Gram (tensor cores in the split precision) in place of the n_b x n_b S_b,
+ * and the same cutoff rule; this equals the block's pseudo-inverse update (F_b = X_b^H eps lies
+ * in the range of S_b, where S_b + diag_shift I and X_b X_b^H + diag_shift I share their
+ * eigenvalues). n_kept_out counts the eigenvalues of S_b + diag_shift I as usual. evals_out
+ * must be NULL for such a step (NQS_ERR_UNSUPPORTED otherwise). sr_step_workspace_size2
+ * sizes the workspace of any sr_step call (it equals sr_step_workspace_size when no block is
+ * solved in sample space). */
+NQS_API int sr_step_workspace_size2(const nqs_model* m, int64_t n_s, const nqs_hamiltonian* h,
+                                    const int64_t* block_off, int32_t n_blocks, double diag_shift, int32_t precision,
+                                    int32_t solver, int32_t flags, size_t* bytes);
 NQS_API int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
             const nqs_hamiltonian* h, const int64_t* block_off, int32_t n_blocks,
             double diag_shift, double cutoff, int32_t cutoff_mode, double eta,

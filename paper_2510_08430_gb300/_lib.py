@@ -24,6 +24,7 @@ NQS_FP64, NQS_FP32, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SPLIT_BF16_EXACT = 0, 
 NQS_RBM, NQS_FFNN = 0, 1
 NQS_SYNC = 1
 NQS_GRAPH = 2
+NQS_PARAM_SPACE = 4
 NQS_SOLVE_FP64, NQS_SOLVE_MIXED, NQS_SOLVE_MIXED_PSD = 0, 1, 2
 NQS_STATIC_MAX_SAMPLES = 65536
 
@@ -58,6 +59,7 @@ SIGNATURES = {
     "qgt_block_build_workspace_size": (C.c_int, [I64, I64, OFF, I32, I32, SZ]),
     "qgt_block_solve_workspace_size": (C.c_int, [OFF, I32, SZ]),
     "sr_step_workspace_size": (C.c_int, [MP, I64, HP, OFF, I32, I32, SZ]),
+    "sr_step_workspace_size2": (C.c_int, [MP, I64, HP, OFF, I32, D, I32, I32, I32, SZ]),
     "qgt_packed_size": (C.c_int64, [OFF, I32]),
     "nqs_jacobian": (C.c_int, [MP, P, P, I64, I32, P, P, I64, P, P]),
     "nqs_local_energy": (C.c_int, [MP, P, P, I64, HP, I32, P, P, P]),

@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16_EXACT, NQS_SPLIT_BF16X3,
-                   NQS_GRAPH, NQS_SYNC, check, nqs_hamiltonian, nqs_model)
+                   NQS_GRAPH, NQS_PARAM_SPACE, NQS_SYNC, check, nqs_hamiltonian, nqs_model)
 
 PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3,
               "split_bf16_exact": NQS_SPLIT_BF16_EXACT}
@@ -291,7 +291,7 @@ class SRStep:
 
     def __init__(self, model: Model, n_s: int, ham: Hamiltonian, block_off, precision="split_bf16x3",
                  diag_shift: float = 1e-3, cutoff: float = 1e-10, cutoff_mode: int = 0, eta: float = 1.0,
-                 want_evals: bool = False, solver="fp64", device="cuda"):
+                 want_evals: bool = False, solver="fp64", device="cuda", param_space: bool = False):
         lib = _lib.load()
         self.model, self.ham = model, ham
         self.n_s = int(n_s)
@@ -301,8 +301,10 @@ class SRStep:
         self.nb = len(self.off) - 1
         self.n_p = int(block_off[-1])
         self.shift, self.cutoff, self.mode, self.eta = float(diag_shift), float(cutoff), int(cutoff_mode), float(eta)
-        self.ws = Workspace(_size(lib.sr_step_workspace_size, C.byref(model.c), self.n_s, C.byref(ham.c), self.off,
-                                  self.nb, self.p), device=device)
+        # blocks wider than n_s are solved in sample space unless param_space is set
+        self.flags = NQS_PARAM_SPACE if param_space else 0
+        self.ws = Workspace(_size(lib.sr_step_workspace_size2, C.byref(model.c), self.n_s, C.byref(ham.c), self.off,
+                                  self.nb, self.shift, self.p, self.solver, self.flags), device=device)
         self.dtheta = torch.empty(self.n_p, dtype=torch.complex128, device=device)
         self.emean = torch.empty(1, dtype=torch.complex128, device=device)
         self.evals = torch.empty(self.n_p, dtype=torch.float64, device=device) if want_evals else None
@@ -326,7 +328,7 @@ class SRStep:
             check(lib.sr_step(C.byref(self.model.c), _ptr(theta), _ptr(configs), self.n_s, C.byref(self.ham.c),
                               self.off, self.nb, self.shift, self.cutoff, self.mode, self.eta, self.p, self.solver,
                               _ptr(self.dtheta), _ptr(self.emean), _ptr(self.evals), _ptr(self.n_kept),
-                              (NQS_SYNC if sync else 0) | _flags, self.ws.h, _stream()))
+                              (NQS_SYNC if sync else 0) | self.flags | _flags, self.ws.h, _stream()))
         return self.dtheta, self.emean
 
     def capture(self, theta: torch.Tensor, configs: torch.Tensor) -> "torch.cuda.CUDAGraph":
@@ -358,10 +360,10 @@ class SRStep:
 
 def sr_step(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian, block_off,
             diag_shift: float, cutoff: float, eta: float = 1.0, precision="fp64", cutoff_mode: int = 0,
-            want_evals: bool = True, solver="fp64"):
+            want_evals: bool = True, solver="fp64", param_space: bool = False):
     """One whole block-layer SR step: (dtheta, Emean, evals, n_kept)."""
     st = SRStep(model, int(configs.shape[0]), ham, block_off, precision, diag_shift, cutoff, cutoff_mode, eta,
-                want_evals, solver, device=configs.device)
+                want_evals, solver, device=configs.device, param_space=param_space)
     st(theta, configs, sync=True)
     return st.dtheta, st.emean, st.evals, st.n_kept
 

@@ -259,6 +259,269 @@ int check_ws(nqs_workspace* ws, const Arena& need) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- blocks wider than the sample count
+// A block with more parameters than samples (n_b > N_s) is solved in sample space by the
+// push-through identity:
+//   dtheta_b = -eta X_b^H pinv(X_b X_b^H + lambda I) eps,  X_b = dO_b / sqrt(N_s), eps = e / sqrt(N_s),
+// an N_s x N_s problem in place of the n_b x n_b one. With lambda > 0 and the same threshold it
+// equals the block's pseudo-inverse update: F_b = X_b^H eps lies in the range of S_b, on which
+// S_b + lambda I and X_b X_b^H + lambda I have the same eigenvalues (the others equal lambda and
+// meet no component of F_b). The narrow blocks keep the parameter-space Gram and solve.
+namespace {
+
+struct WidePlan {
+    int nnar, nwide;
+    int nar[MAXB], wid[MAXB];   // block indices in the caller's order
+    int64_t nar_off[MAXB + 1];  // compact offsets of the narrow blocks
+    long long nar_np;           // parameters in narrow blocks
+    long long max_wide;         // largest wide block
+};
+
+bool is_wide(long long n, long long ns, double shift, int prec, int solver, int flags) {
+    return n > ns && shift > 0.0 && solver != NQS_SOLVE_FP64 && prec != NQS_FP32 && prec != NQS_SPLIT_BF16 &&
+           prec != NQS_SPLIT_BF16X3 && (flags & NQS_PARAM_SPACE) == 0;
+}
+
+void wide_plan(const int64_t* off, int nb, long long ns, double shift, int prec, int solver, int flags,
+               WidePlan* wp) {
+    wp->nnar = wp->nwide = 0;
+    wp->nar_np = 0;
+    wp->max_wide = 0;
+    wp->nar_off[0] = 0;
+    for (int b = 0; b < nb; ++b) {
+        const long long n = off[b + 1] - off[b];
+        if (is_wide(n, ns, shift, prec, solver, flags)) {
+            wp->wid[wp->nwide++] = b;
+            wp->max_wide = n > wp->max_wide ? n : wp->max_wide;
+        } else {
+            wp->nar[wp->nnar++] = b;
+            wp->nar_np += n;
+            wp->nar_off[wp->nnar] = wp->nar_np;
+        }
+    }
+}
+
+struct WideBufs {
+    JacBufs jb, jbe;
+    ElocBufs eb;
+    void* O;
+    long long ldo;
+    c128 *eloc, *e, *F;
+    // narrow blocks (compact)
+    void* planes[5];
+    double* diag;
+    int8_t* gexp;
+    long long ldk;
+    c128 *S, *Fn, *dthn;
+    int32_t* nkn;
+    // wide blocks (one at a time)
+    void* planesT[5];
+    int8_t* gexpT;
+    double* diagT;
+    void* Y;
+    long long ldkT, ldy;
+    c128 *T, *rhs, *u;
+    int32_t* keptT;
+    void* solve;
+    size_t solve_bytes;
+};
+
+void plan_wide(Arena& a, const ModelDesc& md, long long ns, int nbonds, const int64_t* off, int nb, int prec,
+               const WidePlan& wp, WideBufs* w) {
+    plan_model(a, md, ns, jac_prec(prec), &w->jb, true);
+    if (eloc_prec(prec) != jac_prec(prec)) plan_model(a, md, ns, eloc_prec(prec), &w->jbe, false);
+    else w->jbe = w->jb;
+    plan_eloc(a, md, ns, nbonds, &w->eb);
+    w->ldo = round_up(ns, 32);
+    w->O = a.take(csize(prec) * (size_t)md.n_p * (size_t)w->ldo);
+    w->eloc = static_cast<c128*>(a.take(16 * ns));
+    w->e = static_cast<c128*>(a.take(16 * ns));
+    w->F = static_cast<c128*>(a.take(16 * (size_t)md.n_p));
+    const int nsp = nsplit_of(prec);
+    w->ldk = round_up(ns, 64);
+    const long long nn = wp.nar_np > 0 ? wp.nar_np : 1;
+    for (int q = 0; q < 5; ++q) w->planes[q] = q < nsp ? a.take(2ull * 2 * nn * w->ldk) : nullptr;
+    w->diag = nsp ? static_cast<double*>(a.take(8 * nn)) : nullptr;
+    w->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(w->ldk / GRAM_GROUP) * nn)) : nullptr;
+    long long sq = 0;
+    for (int i = 0; i < wp.nnar; ++i) {
+        const long long n = off[wp.nar[i] + 1] - off[wp.nar[i]];
+        sq += n * n;
+    }
+    w->S = static_cast<c128*>(a.take(16 * (size_t)(sq > 0 ? sq : 1)));
+    w->Fn = static_cast<c128*>(a.take(16 * nn));
+    w->dthn = static_cast<c128*>(a.take(16 * nn));
+    w->nkn = static_cast<int32_t*>(a.take(4 * MAXB));
+    w->ldkT = round_up(wp.max_wide, 64);
+    w->ldy = round_up(wp.max_wide, 32);
+    for (int q = 0; q < 5; ++q) w->planesT[q] = q < nsp ? a.take(2ull * 2 * ns * w->ldkT) : nullptr;
+    w->gexpT = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(w->ldkT / GRAM_GROUP) * ns)) : nullptr;
+    w->diagT = nsp ? static_cast<double*>(a.take(8 * ns)) : nullptr;
+    w->Y = nsp ? nullptr : a.take(16 * (size_t)ns * (size_t)w->ldy);
+    w->T = static_cast<c128*>(a.take(16 * (size_t)ns * (size_t)ns));
+    w->rhs = static_cast<c128*>(a.take(16 * ns));
+    w->u = static_cast<c128*>(a.take(16 * ns));
+    w->keptT = static_cast<int32_t*>(a.take(256));
+    const int64_t offT[2] = {0, ns};
+    size_t sb = solve_workspace_bytes(offT, 1);
+    if (wp.nnar > 0) {
+        const size_t sn = solve_workspace_bytes(wp.nar_off, wp.nnar);
+        sb = sn > sb ? sn : sb;
+    }
+    w->solve_bytes = sb;
+    w->solve = a.take(sb);
+}
+
+__global__ void wide_kept_kernel(const int32_t* __restrict__ keptT, long long ns, long long nb, int32_t* out) {
+    // all N_s eigenvalues of X X^H + lambda I kept (the smallest equals lambda: X is centred)
+    // <=> lambda kept <=> every eigenvalue of S_b + lambda I kept
+    if (threadIdx.x == 0 && out) *out = keptT[0] == ns ? (int32_t)nb : keptT[0];
+}
+
+int run_step_wide(const ModelDesc& md, const HamDesc& hd, const void* theta, const int8_t* configs, long long ns,
+                  const int64_t* off, int nb, double shift, double cutoff, int mode, double eta, int prec,
+                  int solver, c128* dtheta, c128* Emean, int32_t* n_kept, int flags, const WidePlan& wp,
+                  const WideBufs& w, nqs_workspace* ws, DevStatus* status, cudaStream_t st) {
+    const int rp = jac_prec(prec), re = eloc_prec(prec);
+    const bool graph = (flags & NQS_GRAPH) != 0;
+    const bool tm = ws->timing && !graph;
+    const int nsp = nsplit_of(prec);
+    const size_t cs = csize(prec);
+    if (tm) CK(cudaEventRecord(ws->ev[0], st), "event");
+    int rc = run_model(md, rp, theta, configs, ns, w.jb, st);
+    if (rc) return rc;
+    CK(launch_backward(rp, md, w.jb.thR, w.jb.Z, ns, w.jb.G, st), "backward");
+    CK(launch_jac_write(rp, md, w.jb.Z, w.jb.G, configs, ns, w.O, w.ldo, st), "jacobian");
+    if (tm) CK(cudaEventRecord(ws->ev[1], st), "event");
+    if (re != rp) {
+        rc = run_model(md, re, theta, configs, ns, w.jbe, st);
+        if (rc) return rc;
+    }
+    rc = run_eloc(md, re, hd, configs, ns, w.jbe, w.eb, w.eloc, status, st);
+    if (rc) return rc;
+    if (tm) CK(cudaEventRecord(ws->ev[2], st), "event");
+    CK(launch_emean(w.eloc, nullptr, ns, Emean, w.e, status, st), "emean");
+    // centring and force: narrow blocks write their split planes (compact rows); wide blocks
+    // are centred in place (FP64) for the sample-major split and the back-projection
+    char* Ob = static_cast<char*>(w.O);
+    for (int i = 0; i < wp.nnar; ++i) {
+        const int b = wp.nar[i];
+        const long long n = off[b + 1] - off[b], r0 = wp.nar_off[i];
+        void* pl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        for (int q = 0; q < nsp; ++q) pl[q] = static_cast<__nv_bfloat16*>(w.planes[q]) + 2 * r0 * w.ldk;
+        CK(launch_center(prec, nsp, Ob + cs * (size_t)off[b] * (size_t)w.ldo, w.ldo, ns, n, nullptr, w.e,
+                         w.F + off[b], nullptr, nsp ? pl : nullptr, w.ldk, nsp ? w.diag + r0 : nullptr,
+                         nsp == 5 ? w.gexp + r0 : nullptr, wp.nar_np, status, st),
+           "center");
+    }
+    for (int i = 0; i < wp.nwide; ++i) {
+        const int b = wp.wid[i];
+        CK(launch_center(NQS_FP64, 0, Ob + cs * (size_t)off[b] * (size_t)w.ldo, w.ldo, ns, off[b + 1] - off[b],
+                         nullptr, w.e, w.F + off[b], nullptr, nullptr, 0, nullptr, nullptr, 0, status, st),
+           "center");
+    }
+    if (tm) CK(cudaEventRecord(ws->ev[3], st), "event");
+    Arena sa{static_cast<char*>(w.solve), w.solve_bytes, 0};
+    // narrow blocks: parameter-space Gram on compact rows, solve on compact offsets
+    if (wp.nnar > 0) {
+        GramTable* tab = new (std::nothrow) GramTable;
+        if (!tab) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+        tab->nb = wp.nnar;
+        tab->total_tiles = 0;
+        long long so = 0;
+        for (int i = 0; i < wp.nnar; ++i) {
+            const int b = wp.nar[i];
+            const long long n = off[b + 1] - off[b], T = (n + 63) / 64;
+            GBlk& g = tab->b[i];
+            g.row0 = nsp ? wp.nar_off[i] : off[b];
+            g.s_off = so;
+            g.n = (int)n;
+            g.tiles = (int)(T * (T + 1) / 2);
+            g.tile0 = tab->total_tiles;
+            g.scale = 0.0;
+            tab->total_tiles += T * (T + 1) / 2;
+            so += n * n;
+        }
+        cudaError_t e;
+        if (nsp) {
+            e = launch_gram_tc(nsp, w.planes, w.gexp, wp.nar_np, 2 * wp.nar_np, w.ldk, w.ldk, 1.0 / (double)ns, *tab,
+                               w.S, status, st);
+            if (e == cudaSuccess) e = launch_set_diag(w.S, *tab, w.diag, st);
+        } else {
+            e = launch_gram_simt(prec, w.O, w.ldo, ns, nullptr, 1.0 / (double)ns, *tab, w.S, st);
+        }
+        delete tab;
+        if (e == cudaErrorNotSupported) return fail(NQS_ERR_UNSUPPORTED, "tensor-core Gram needs an sm_103 device");
+        CK(e, "gram");
+        for (int i = 0; i < wp.nnar; ++i) {
+            const int b = wp.nar[i];
+            CK(cudaMemcpyAsync(w.Fn + wp.nar_off[i], w.F + off[b], 16 * (size_t)(off[b + 1] - off[b]),
+                               cudaMemcpyDeviceToDevice, st),
+               "gather F");
+        }
+        int32_t* nk = n_kept ? w.nkn : nullptr;
+        Arena sa2 = sa;
+        rc = run_solve(w.S, wp.nar_off, wp.nnar, w.Fn, shift, cutoff, mode, eta,
+                       solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver, w.dthn, nullptr, nk, sa2, status, st,
+                       nullptr, nullptr, graph);
+        if (rc) return rc;
+        for (int i = 0; i < wp.nnar; ++i) {
+            const int b = wp.nar[i];
+            CK(cudaMemcpyAsync(dtheta + off[b], w.dthn + wp.nar_off[i], 16 * (size_t)(off[b + 1] - off[b]),
+                               cudaMemcpyDeviceToDevice, st),
+               "scatter dtheta");
+            if (nk) CK(cudaMemcpyAsync(n_kept + b, nk + i, 4, cudaMemcpyDeviceToDevice, st), "n_kept");
+        }
+    }
+    // wide blocks, one at a time: sample-space Gram, solve, back-projection
+    const int64_t offT[2] = {0, ns};
+    for (int i = 0; i < wp.nwide; ++i) {
+        const int b = wp.wid[i];
+        const long long n = off[b + 1] - off[b];
+        const c128* dOb = reinterpret_cast<const c128*>(Ob + cs * (size_t)off[b] * (size_t)w.ldo);
+        GramTable* tab = new (std::nothrow) GramTable;
+        if (!tab) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+        gram_table(offT, 1, 64, tab);
+        cudaError_t e;
+        if (nsp) {
+            e = launch_transpose_group(dOb, w.ldo, ns, n, w.planesT, w.gexpT, w.ldkT, w.diagT, st);
+            if (e == cudaSuccess)
+                e = launch_gram_tc(nsp, w.planesT, w.gexpT, ns, 2 * ns, w.ldkT, w.ldkT, 1.0 / (double)ns, *tab, w.T,
+                                   status, st);
+            if (e == cudaSuccess) e = launch_set_diag(w.T, *tab, w.diagT, st);
+        } else {
+            e = launch_ntk_transpose(NQS_FP64, dOb, w.ldo, ns, n, w.Y, w.ldy, st);
+            if (e == cudaSuccess) e = launch_gram_simt(NQS_FP64, w.Y, w.ldy, w.ldy, nullptr, 1.0 / (double)ns, *tab,
+                                                       w.T, st);
+        }
+        delete tab;
+        if (e == cudaErrorNotSupported) return fail(NQS_ERR_UNSUPPORTED, "tensor-core Gram needs an sm_103 device");
+        CK(e, "sample-space gram");
+        // the Gram kernels give conj(X X^H): solve (conj(X X^H) + lambda I) u = conj(eps), then
+        // dtheta_b = -eta X^H conj(u)
+        CK(launch_ntk_rhs(w.e, ns, w.rhs, st), "rhs");
+        Arena sa2 = sa;
+        rc = run_solve(w.T, offT, 1, w.rhs, shift, cutoff, mode, -1.0, NQS_SOLVE_MIXED_PSD, w.u, nullptr, w.keptT, sa2,
+                       status, st, nullptr, nullptr, graph);
+        if (rc) return rc;
+        CK(launch_ntk_back(dOb, w.ldo, ns, n, w.u, eta, dtheta + off[b], st), "back-projection");
+        if (n_kept) {
+            count_launch();
+            wide_kept_kernel<<<1, 32, 0, st>>>(w.keptT, ns, n, n_kept + b);
+            CK(cudaGetLastError(), "n_kept");
+        }
+    }
+    if (tm) {
+        CK(cudaEventRecord(ws->ev[4], st), "event");
+        CK(cudaEventRecord(ws->ev[5], st), "event");
+        CK(cudaEventRecord(ws->ev[6], st), "event");
+        ws->recorded = true;
+    }
+    return NQS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* nqs_last_error(void) { return g_err.c_str(); }
@@ -427,6 +690,29 @@ int sr_step_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonia
     c128 *eloc, *F, *S;
     plan_step(a, md, n_s, h->n_bonds, block_off, n_blocks, precision, &jb, &jbe, &eb, &bb, &O, &ldo, &eloc, &F, &S);
     a.take(solve_workspace_bytes(block_off, n_blocks));
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+int sr_step_workspace_size2(const nqs_model* m, int64_t n_s, const nqs_hamiltonian* h, const int64_t* block_off,
+                            int32_t n_blocks, double diag_shift, int32_t precision, int32_t solver, int32_t flags,
+                            size_t* bytes) {
+    ModelDesc md;
+    if (!bytes || n_s < 1 || !h || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
+    if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    int rc = check_offsets(block_off, n_blocks, md.n_p);
+    if (rc) return rc;
+    WidePlan* wp = new (std::nothrow) WidePlan;
+    if (!wp) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+    wide_plan(block_off, n_blocks, n_s, diag_shift, precision, solver, flags, wp);
+    if (wp->nwide == 0) {
+        delete wp;
+        return sr_step_workspace_size(m, n_s, h, block_off, n_blocks, precision, bytes);
+    }
+    Arena a = sizing_arena();
+    WideBufs wb;
+    plan_wide(a, md, n_s, h->n_bonds, block_off, n_blocks, precision, *wp, &wb);
+    delete wp;
     *bytes = a.used + STATUS_BYTES;
     return NQS_OK;
 }
@@ -685,6 +971,36 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     if (rc) return rc;
     rc = check_offsets(block_off, n_blocks, md.n_p);
     if (rc) return rc;
+    const bool graph = (flags & NQS_GRAPH) != 0;
+    if (graph && (flags & NQS_SYNC)) return fail(NQS_ERR_INVALID_ARG, "NQS_GRAPH cannot be combined with NQS_SYNC");
+    {
+        WidePlan* wp = new (std::nothrow) WidePlan;
+        if (!wp) return fail(NQS_ERR_INVALID_ARG, "host allocation failed");
+        wide_plan(block_off, n_blocks, n_s, diag_shift, precision, solver, flags, wp);
+        if (wp->nwide > 0) {
+            if (solver != NQS_SOLVE_MIXED && solver != NQS_SOLVE_MIXED_PSD) {
+                delete wp;
+                return fail(NQS_ERR_INVALID_ARG, "unknown solver %d", solver);
+            }
+            if (evals_out) {
+                delete wp;
+                return fail(NQS_ERR_UNSUPPORTED, "eigenvalues of a block wider than N_s: call with NQS_PARAM_SPACE");
+            }
+            Arena a = arena_of(ws);
+            WideBufs wb;
+            plan_wide(a, md, n_s, hd.n_bonds, block_off, n_blocks, precision, *wp, &wb);
+            rc = check_ws(ws, a);
+            if (!rc)
+                rc = run_step_wide(md, hd, theta, configs, n_s, block_off, n_blocks, diag_shift, cutoff, cutoff_mode,
+                                   eta, precision, solver, static_cast<c128*>(dtheta_out), static_cast<c128*>(Emean_out),
+                                   n_kept_out, flags, *wp, wb, ws, status_of(ws), static_cast<cudaStream_t>(stream));
+            delete wp;
+            if (rc) return rc;
+            if (flags & NQS_SYNC) return nqs_sync_status(ws, stream);
+            return NQS_OK;
+        }
+        delete wp;
+    }
     Arena a = arena_of(ws);
     JacBufs jb, jbe;
     ElocBufs eb;
@@ -700,8 +1016,6 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DevStatus* status = status_of(ws);
     const int rp = jac_prec(precision), re = eloc_prec(precision);
-    const bool graph = (flags & NQS_GRAPH) != 0;
-    if (graph && (flags & NQS_SYNC)) return fail(NQS_ERR_INVALID_ARG, "NQS_GRAPH cannot be combined with NQS_SYNC");
     const bool tm = ws->timing && !graph;
     if (tm) CK(cudaEventRecord(ws->ev[0], st), "event");
     rc = run_model(md, rp, theta, configs, n_s, jb, st);

@@ -360,6 +360,79 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
     }
 }
 
+// Sample-major grouped error-free split of a centred block (sample-space Gram of a block
+// wider than the sample count): for dO (c128, parameter-major [n_b][ldo], already centred)
+// the planes hold rows 2s = Re dO(s), 2s+1 = Im dO(s) along the block's parameters k
+// (ldk >= n_b, zero beyond n_b), split into five BF16 slices exactly as center_group_kernel
+// does along samples, with one exponent per (sample, group of GROUP parameters):
+// gexp[k / GROUP][s]. diag[s] += sum_k |dO_k(s)|^2 / ns (FP64; diag zeroed by the caller).
+// One CTA per 32 x 32 (parameter, sample) tile; warp w takes samples w, w + 8, w + 16, w + 24
+// of the tile, lane r its parameter k0 + r.
+__global__ void __launch_bounds__(256) transpose_group_kernel(const c128* __restrict__ dO, long long ldo, long long ns,
+                                                               long long nb, __nv_bfloat16* __restrict__ pl0,
+                                                               __nv_bfloat16* __restrict__ pl1,
+                                                               __nv_bfloat16* __restrict__ pl2,
+                                                               __nv_bfloat16* __restrict__ pl3,
+                                                               __nv_bfloat16* __restrict__ pl4,
+                                                               int8_t* __restrict__ gexp, long long ldk,
+                                                               double* __restrict__ diag) {
+    __shared__ c128 t[32][33];
+    const long long s0 = (long long)blockIdx.x * 32, k0 = (long long)blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r = wid; r < 32; r += 8) {
+        const long long k = k0 + r, s = s0 + lane;
+        t[r][lane] = (k < nb && s < ns) ? dO[k * ldo + s] : mk<double>(0.0, 0.0);
+    }
+    __syncthreads();
+    __nv_bfloat16* pls[5] = {pl0, pl1, pl2, pl3, pl4};
+    const double inv_ns = 1.0 / (double)ns;
+    for (int c = wid; c < 32; c += 8) {
+        const long long s = s0 + c;
+        if (s >= ns) continue;  // warp-uniform
+        const c128 v = t[lane][c];
+        const double dr = v.re, di = v.im;
+        double mx = fmax(fabs(dr), fabs(di));
+        double d2 = dr * dr + di * di;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        }
+        int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
+        ex = mx > 0.0 ? ex : 0;
+        ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
+        if (lane == 0) {
+            gexp[(k0 / GROUP) * ns + s] = (int8_t)ex;
+            if (d2 != 0.0) atomicAdd(diag + s, d2 * inv_ns);
+        }
+        const double sc = __longlong_as_double((long long)(1023 + 39 - ex) << 52);  // 2^(39 - E)
+        int dr5[5], di5[5];
+        digits5(__double2ll_rn(dr * sc), dr5);
+        digits5(__double2ll_rn(di * sc), di5);
+        const float qs[5] = {0x1p-7f, 0x1p-15f, 0x1p-23f, 0x1p-31f, 0x1p-39f};
+        const long long k = k0 + lane;
+        if (k < ldk) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                pls[q][(2 * s) * ldk + k] = __float2bfloat16_rn((float)dr5[q] * qs[q]);
+                pls[q][(2 * s + 1) * ldk + k] = __float2bfloat16_rn((float)di5[q] * qs[q]);
+            }
+        }
+    }
+}
+
+cudaError_t launch_transpose_group(const c128* dO, long long ldo, long long ns, long long nb, void* const* planes,
+                                   int8_t* gexp, long long ldk, double* diag, cudaStream_t st) {
+    if (ldk % 64 != 0 || ldk < nb) return cudaErrorInvalidValue;
+    if (cudaMemsetAsync(diag, 0, sizeof(double) * ns, st) != cudaSuccess) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((ns + 31) / 32), (unsigned)(ldk / 32));
+    count_launch();
+    transpose_group_kernel<<<grid, 256, 0, st>>>(dO, ldo, ns, nb, (__nv_bfloat16*)planes[0], (__nv_bfloat16*)planes[1],
+                                                 (__nv_bfloat16*)planes[2], (__nv_bfloat16*)planes[3],
+                                                 (__nv_bfloat16*)planes[4], gexp, ldk, diag);
+    return cudaGetLastError();
+}
+
 // out[k] = sum_s conj(O[k][s]) g[s] (vector-Jacobian product of ln psi, FP64 accumulation).
 template <typename R>
 __global__ void __launch_bounds__(256) vjp_kernel(const cx<R>* __restrict__ O, long long ldo, long long ns,

@@ -80,6 +80,11 @@ cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c1
 // means[0..np) = osum / n_total, means[np] = esum[0] / n_total (global means of a sharded step)
 cudaError_t launch_sums_to_means(const c128* osum, const c128* esum, long long np, long long n_total, c128* means,
                                  cudaStream_t st);
+// sample-major grouped split of a centred block (c128 dO [nb][ldo]) for the sample-space Gram:
+// planes[q] rows 2s, 2s+1 along ldk (multiple of 64) parameters, gexp[k / GRAM_GROUP][s],
+// diag[s] = sum_k |dO_k(s)|^2 / ns
+cudaError_t launch_transpose_group(const c128* dO, long long ldo, long long ns, long long nb, void* const* planes,
+                                   int8_t* gexp, long long ldk, double* diag, cudaStream_t st);
 // sample-space (NTK) comparator
 cudaError_t launch_ntk_transpose(int prec, const c128* O, long long ldo, long long ns, long long np, void* Y,
                                  long long ldy, cudaStream_t st);

@@ -50,7 +50,9 @@ def test_batched_equals_separate_steps(prec, solver, tol):
                                            prec, solver=solver)
     k = 0
     for j, (w, (model, theta, x, ham)) in enumerate(zip(ws, ins)):
-        d1, e1, _, n1 = nq().sr_step(model, theta, x, ham, w.block_off, 1e-3, 1e-10, 1.0, prec, solver=solver)
+        # the batched step forms every S_b in parameter space: compare with the same form
+        d1, e1, _, n1 = nq().sr_step(model, theta, x, ham, w.block_off, 1e-3, 1e-10, 1.0, prec, solver=solver,
+                                     param_space=True)
         assert rel(dths[j].cpu().numpy(), d1.cpu().numpy()) < tol, w.name
         assert abs(em[j].item() - e1.cpu().numpy()[0]) <= 1e-12 * abs(e1.cpu().numpy()[0])
         nbj = len(w.block_off) - 1

@@ -281,10 +281,56 @@ def test_sr_step_mixed_solver(name, ns, prec, tol):
     w = W.make_workload(name, ns)
     model, theta, x, ham = dev_inputs(w)
     dth, em, ev, nk = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec,
-                                   solver="mixed")
+                                   solver="mixed", want_evals=False)
     r = _oracle_all(w)
     assert rel(dth.cpu().numpy(), r["dtheta"]) < tol
     assert np.array_equal(nk.cpu().numpy(), r["n_kept"])
+
+
+@pytest.mark.parametrize("name,ns,prec,tol", [
+    ("j1j2_6x6_ffnn", 300, "fp64", 1e-10),
+    ("j1j2_6x6_ffnn", 300, "split_bf16_exact", 1e-6),
+    ("chain10_rbm", 64, "fp64", 1e-10),
+])
+def test_sample_space_blocks_match_oracle(name, ns, prec, tol):
+    """Blocks wider than the sample count (2368 and 4160 parameters at 300 samples; the RBM's
+    100 weights at 64 samples) are solved in sample space by the push-through identity: the
+    step equals the oracle's eigen-decomposition definition, and the parameter-space form of
+    the same step."""
+    w = W.make_workload(name, ns)
+    assert max(np.diff(w.block_off)) > ns
+    model, theta, x, ham = dev_inputs(w)
+    dth, em, _, nk = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec,
+                                  solver="mixed", want_evals=False)
+    r = _oracle_all(w)
+    assert rel(dth.cpu().numpy(), r["dtheta"]) < tol
+    assert np.array_equal(nk.cpu().numpy(), r["n_kept"])
+    assert abs(em.cpu().numpy()[0] - r["e_mean"]) < 1e-12 * abs(r["e_mean"])
+    dp, _, _, nkp = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec,
+                                 solver="mixed", want_evals=False, param_space=True)
+    assert rel(dth.cpu().numpy(), dp.cpu().numpy()) < tol
+    assert np.array_equal(nk.cpu().numpy(), nkp.cpu().numpy())
+
+
+@pytest.mark.parametrize("cutoff,mode", [(1e-3, 0), (3e-6, 1)])
+def test_sample_space_block_with_binding_cutoff(cutoff, mode):
+    """A binding cutoff on a block wider than the sample count: the sample-space eigen
+    solve with the same threshold still equals the definition, and n_kept counts the
+    eigenvalues of S_b + lambda I (the lambda eigenvalues of the null space included)."""
+    model = W.Model(W.FFNN, (16, 24, 8, 1))
+    rng = np.random.default_rng(31)
+    theta = W.init_params(model, rng)
+    xs = W.zero_sz_configs(16, 100, rng)
+    ij, jj = W.square_j1j2_bonds(4, 4, 1.0, 0.4)
+    w = W.Workload("ffnn4x4_cut", model, theta, xs, ij, jj, model.block_offsets(), 1e-6, cutoff, "fp64")
+    m, th, x, ham = dev_inputs(w)
+    dth, _, _, nk = nq().sr_step(m, th, x, ham, w.block_off, w.diag_shift, cutoff, 1.0, "fp64", cutoff_mode=mode,
+                                 solver="mixed", want_evals=False)
+    r = oracle.qgt.sr_step(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.block_off, w.diag_shift, cutoff,
+                           absolute=mode == 1)
+    assert r["n_kept"].min() < np.diff(w.block_off).max()  # the cutoff binds
+    assert np.array_equal(nk.cpu().numpy(), r["n_kept"])
+    assert rel(dth.cpu().numpy(), r["dtheta"]) < 1e-8
 
 
 def _golden(name):

@@ -33,7 +33,8 @@ def test_simulated_ranks_equal_unsharded_step(name, ns, prec, solver, tol):
     shards = [x[idx] for idx in np.array_split(np.arange(ns), 3)]
     be = sharded.LibraryShardBackend(model, ham, w.block_off, prec, solver)
     dth, em = sharded.step_simulated(be, theta, shards, w.block_off, w.diag_shift, w.cutoff)
-    d1, e1, _, _ = nq.sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec, solver=solver)
+    d1, e1, _, _ = nq.sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec, solver=solver,
+                              want_evals=False, param_space=True)
     assert rel(dth.cpu().numpy(), d1.cpu().numpy()) < tol
     r = oracle.qgt.sr_step(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.block_off, w.diag_shift, w.cutoff,
                            1.0, w.c, w.sign_rule)
