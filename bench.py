@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--param-space", action="store_true",
+                    help="solve every block in parameter space (profiling of reduced-N_s cases with the "
+                         "full-size kernels)")
     ap.add_argument("--sharded", action="store_true",
                     help="split ONE instance over the ranks by samples (three exchanges over NCCL; strong scaling)")
     return ap.parse_args()
@@ -385,7 +388,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     theta = torch.as_tensor(w.theta, device="cuda")
     x = torch.as_tensor(w.configs, device="cuda")
     ham = nq.Hamiltonian(w.model.n_sites, w.bond_ij, w.bond_j, w.c, w.sign_rule)
-    step = nq.SRStep(model, w.n_samples, ham, w.block_off, w.precision, w.diag_shift, w.cutoff, solver=args.solver)
+    step = nq.SRStep(model, w.n_samples, ham, w.block_off, w.precision, w.diag_shift, w.cutoff, solver=args.solver,
+                     param_space=args.param_space)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():

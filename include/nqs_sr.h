@@ -383,6 +383,27 @@ NQS_API int sr_step_batched(int32_t n_inst, const nqs_model* models, const void*
                     double* evals_out, int32_t* n_kept_out, int32_t flags, nqs_workspace* ws,
                     void* stream);
 
+/* ---- inverse-metric diagnostics (Eq. 4; Sec. 3, Table 1) ----
+ * nqs_born_weights -- w_out[s] = |psi(x_s)|^2 / sum_t |psi(x_t)|^2 from logpsi (c128 [n]):
+ *   the sample weights that turn an enumeration of all 2^N configurations into exact
+ *   expectations (qgt_block_build with these weights gives the exact QGT). float64 [n] out.
+ * qgt_inverse_diagnostics -- with A = pinv(S_a' + diag_shift I) and B = pinv(S_b + diag_shift I),
+ *   S_a' the restriction of S_a to the diagonal blocks of block_off_a (the block-layer QGT of
+ *   a full QGT; n_blocks_a = 1 keeps all of S_a), and the cutoff rule of qgt_block_solve:
+ *     out[0] = F(A, B)     = Tr[A^H B] / (|A|_F |B|_F)            (Frobenius overlap)
+ *     out[1] = eps_F(A, B) = |A - B|_F / |B|_F                     (relative Frobenius error)
+ *     out[2] = kappa(A), out[3] = kappa(B): largest over smallest kept eigenvalue
+ *     out[4] = r_lambda(A, B): Pearson correlation of the spectra of A and B, each in
+ *              descending order (eigenvalues cut by the pseudo-inverse count as 0).
+ *   S_a, S_b: c128 n x n row-major, lower triangle used (DEVICE); out: DEVICE float64 [5].
+ *   FP64 eigen-decompositions with eigenvectors (Householder, implicit QL); n <= 12000.
+ *   Workspace: qgt_inverse_diagnostics_workspace_size (about 64 n^2 bytes). */
+NQS_API int nqs_born_weights(const void* logpsi, int64_t n, double* w_out, void* stream);
+NQS_API int qgt_inverse_diagnostics_workspace_size(int64_t n, size_t* bytes);
+NQS_API int qgt_inverse_diagnostics(const void* S_a, const int64_t* block_off_a, int32_t n_blocks_a,
+                                    const void* S_b, int64_t n, double diag_shift, double cutoff,
+                                    int32_t cutoff_mode, double* out, nqs_workspace* ws, void* stream);
+
 /* ---- measurement hooks ----
  * nqs_stage_timing(ws, 1) makes later sr_step calls on `ws` record CUDA events
  * on their stream at the stage boundaries: [0] Jacobian (parameter conversion,

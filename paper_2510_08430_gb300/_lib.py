@@ -79,6 +79,9 @@ SIGNATURES = {
     "nqs_stage_times": (C.c_int, [P, C.POINTER(C.c_double), I32, C.POINTER(C.c_int32)]),
     "nqs_launch_count": (C.c_int64, []),
     "nqs_set_limits": (C.c_int, [I32, I64]),
+    "nqs_born_weights": (C.c_int, [P, I64, P, P]),
+    "qgt_inverse_diagnostics_workspace_size": (C.c_int, [I64, SZ]),
+    "qgt_inverse_diagnostics": (C.c_int, [P, OFF, I32, P, I64, D, D, I32, P, P, P]),
 }
 
 _lib = None

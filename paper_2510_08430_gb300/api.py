@@ -418,6 +418,64 @@ def ntk_solve(O: torch.Tensor, n_s: int, eloc: torch.Tensor, diag_shift: float, 
     return dth, em
 
 
+def born_weights(logpsi: torch.Tensor) -> torch.Tensor:
+    """|psi|^2 / Z over the given configurations (nqs_born_weights), float64 [n]."""
+    w = torch.empty(int(logpsi.shape[0]), dtype=torch.float64, device=logpsi.device)
+    with _on(logpsi):
+        check(_lib.load().nqs_born_weights(_ptr(logpsi), int(logpsi.shape[0]), _ptr(w), _stream()))
+    return w
+
+
+def qgt_inverse_diagnostics(S_a: torch.Tensor, block_off_a, S_b: torch.Tensor, diag_shift: float, cutoff: float,
+                            cutoff_mode: int = 0) -> dict:
+    """Eq. 4 diagnostics of A = pinv(blocks of S_a + shift I) against B = pinv(S_b + shift I)
+    (S_a, S_b: n x n complex128, lower triangle used)."""
+    lib = _lib.load()
+    n = int(S_b.shape[-1])
+    off = _off(block_off_a)
+    ws = Workspace(_size(lib.qgt_inverse_diagnostics_workspace_size, n), device=S_b.device)
+    out = torch.empty(5, dtype=torch.float64, device=S_b.device)
+    Sa, Sb = S_a.contiguous(), S_b.contiguous()
+    with _on(Sa, Sb):
+        check(lib.qgt_inverse_diagnostics(_ptr(Sa), off, len(off) - 1, _ptr(Sb), n, float(diag_shift), float(cutoff),
+                                          int(cutoff_mode), _ptr(out), ws.h, _stream()))
+    ws.sync_status()
+    v = out.cpu().tolist()
+    return {"F": v[0], "eps_F": v[1], "kappa_A": v[2], "kappa_B": v[3], "r_lambda": v[4]}
+
+
+def inverse_metric_study(model: Model, theta: torch.Tensor, configs: torch.Tensor, block_off, diag_shift: float,
+                         cutoff: float) -> dict:
+    """Eq. 4 diagnostics on a system small enough to enumerate (N <= 12 sites): B is the
+    pseudo-inverse of the exact QGT (all 2^N configurations, Born weights); A that of
+    (i) the block-layer QGT of the sampled QGT, (ii) the full sampled QGT, (iii) the
+    block-layer QGT of the exact QGT. Every number is computed by the library."""
+    n_sites = model.widths[0]
+    if n_sites > 12:
+        raise ValueError("enumeration limited to 12 sites")
+    dev = configs.device
+    idx = torch.arange(2 ** n_sites, device=dev)
+    bits = (idx[:, None] >> torch.arange(n_sites - 1, -1, -1, device=dev)[None, :]) & 1
+    x_all = (2 * bits - 1).to(torch.int8).contiguous()
+    n_p = int(np.asarray(block_off)[-1])
+    full = np.array([0, n_p], dtype=np.int64)
+
+    def full_qgt(x, w):
+        lp, O = nqs_jacobian(model, theta, x, "fp64")
+        zero = torch.zeros(int(x.shape[0]), dtype=torch.complex128, device=dev)
+        S, _, _, _ = qgt_block_build(O, int(x.shape[0]), full, zero, "fp64", w=w)
+        return S.view(n_p, n_p), lp
+
+    lp_all, _ = nqs_jacobian(model, theta, x_all, "fp64")
+    S_exact, _ = full_qgt(x_all, born_weights(lp_all))
+    S_samp, _ = full_qgt(configs, None)
+    return {
+        "block_sampled_vs_exact": qgt_inverse_diagnostics(S_samp, block_off, S_exact, diag_shift, cutoff),
+        "full_sampled_vs_exact": qgt_inverse_diagnostics(S_samp, full, S_exact, diag_shift, cutoff),
+        "block_exact_vs_exact": qgt_inverse_diagnostics(S_exact, block_off, S_exact, diag_shift, cutoff),
+    }
+
+
 def set_limits(max_sweeps: int = 0, wait_ns: int = 0) -> None:
     """Test hook of the failure paths (nqs_set_limits): lower the eigen-solver and refinement
     sweep limits and the device wait budget of the persistent solver kernels; 0 restores

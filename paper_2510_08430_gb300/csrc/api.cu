@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cuda_bf16.h>
 #include "internal.cuh"
+#include "eigh.cuh"
 
 using namespace nqs;
 
@@ -1279,6 +1280,78 @@ extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const vo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- inverse-metric diagnostics
+namespace {
+struct DiagPlan {
+    c128 *Sa, *Sb, *Ua, *Ub;
+    long long* blk_of;
+    double *sig_a, *sig_b, *ev_a, *ev_b, *partial;
+    void* eig;
+    size_t eig_bytes;
+};
+void plan_diag(Arena& a, long long n, DiagPlan* d) {
+    d->Sa = static_cast<c128*>(a.take(16 * (size_t)n * n));
+    d->Sb = static_cast<c128*>(a.take(16 * (size_t)n * n));
+    d->Ua = static_cast<c128*>(a.take(16 * (size_t)n * n));
+    d->Ub = static_cast<c128*>(a.take(16 * (size_t)n * n));
+    d->blk_of = static_cast<long long*>(a.take(8 * (size_t)n));
+    d->sig_a = static_cast<double*>(a.take(8 * (size_t)n));
+    d->sig_b = static_cast<double*>(a.take(8 * (size_t)n));
+    d->ev_a = static_cast<double*>(a.take(8 * (size_t)n));
+    d->ev_b = static_cast<double*>(a.take(8 * (size_t)n));
+    const long long T = (n + 31) / 32;
+    d->partial = static_cast<double*>(a.take(8 * (size_t)(2 + T * T)));
+    d->eig_bytes = eig_vectors_workspace_bytes(n);
+    d->eig = a.take(d->eig_bytes);
+}
+}  // namespace
+
+extern "C" int nqs_born_weights(const void* logpsi, int64_t n, double* w_out, void* stream) {
+    if (!logpsi || !w_out || n < 1) return fail(NQS_ERR_INVALID_ARG, "nqs_born_weights: bad arguments");
+    CK(launch_born_weights(static_cast<const c128*>(logpsi), n, w_out, static_cast<cudaStream_t>(stream)),
+       "born weights");
+    return NQS_OK;
+}
+
+extern "C" int qgt_inverse_diagnostics_workspace_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 1) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
+    Arena a = sizing_arena();
+    DiagPlan d;
+    plan_diag(a, n, &d);
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+extern "C" int qgt_inverse_diagnostics(const void* S_a, const int64_t* block_off_a, int32_t n_blocks_a,
+                                       const void* S_b, int64_t n, double diag_shift, double cutoff,
+                                       int32_t cutoff_mode, double* out, nqs_workspace* ws, void* stream) {
+    if (!S_a || !S_b || !out || n < 1) return fail(NQS_ERR_INVALID_ARG, "qgt_inverse_diagnostics: bad arguments");
+    if (!(diag_shift >= 0.0) || !(cutoff >= 0.0) || (cutoff_mode != 0 && cutoff_mode != 1))
+        return fail(NQS_ERR_INVALID_ARG, "qgt_inverse_diagnostics: bad shift, cutoff or mode");
+    int rc = check_offsets(block_off_a, n_blocks_a, n);
+    if (rc) return rc;
+    if (n > QL_MAXN) return fail(NQS_ERR_UNSUPPORTED, "qgt_inverse_diagnostics: n = %lld above %d", (long long)n,
+                                 QL_MAXN);
+    Arena a = arena_of(ws);
+    DiagPlan d;
+    plan_diag(a, n, &d);
+    rc = check_ws(ws, a);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* status = status_of(ws);
+    CK(launch_block_restrict(static_cast<const c128*>(S_a), n, block_off_a, n_blocks_a, d.Sa, d.blk_of, st),
+       "block restriction");
+    CK(cudaMemcpyAsync(d.Sb, S_b, 16 * (size_t)n * n, cudaMemcpyDeviceToDevice, st), "copy");
+    rc = launch_eig_vectors(d.Sa, n, diag_shift, d.sig_a, d.ev_a, d.Ua, d.eig, d.eig_bytes, status, st);
+    if (rc) return fail(rc, "eigen-decomposition of S_a failed");
+    rc = launch_eig_vectors(d.Sb, n, diag_shift, d.sig_b, d.ev_b, d.Ub, d.eig, d.eig_bytes, status, st);
+    if (rc) return fail(rc, "eigen-decomposition of S_b failed");
+    CK(launch_inverse_diagnostics(n, d.sig_a, d.ev_a, d.Ua, d.sig_b, d.ev_b, d.Ub, cutoff, cutoff_mode, d.partial,
+                                  out, st),
+       "diagnostics");
+    return NQS_OK;
+}
 
 // ---------------------------------------------------------------- build without a workspace
 // qgt_block_build_static serves callers that cannot lend the library device memory (a

@@ -30,7 +30,9 @@ constexpr int CTE = CT * CT;           // elements per tile
 constexpr int CP = 256;                // threads per CTA
 constexpr int LDT = CT + 1;            // padded leading dimension of shared tiles
 constexpr int CHOL_MAXT = 1024;        // tiles per block edge (n <= 65536)
-constexpr double CHOL_TOL = 1e-14;     // ||r|| <= CHOL_TOL ||F||
+constexpr double CHOL_TOL = 1e-14;     // ||r|| <= CHOL_TOL ||F||, or
+constexpr double CHOL_FLOOR = 1e-12;   // ||r|| <= CHOL_FLOOR ||F|| once ||r|| stops contracting (the
+                                       // FP64 residual's rounding floor, ~n u ||S~|| ||x||)
 constexpr double PSD_MARGIN = 1e-6;    // rounding of a Gram matrix's eigenvalues, relative to ||S||
 
 enum : int { CF_CERT = 1, CF_PIVOT = 2, CF_CONV = 4, CF_NONFINITE = 8 };
@@ -59,7 +61,7 @@ struct CBufs {
     c128* P;                 // residual partials: P[poff + i T + j][CT] = (S~ x) part of row tile i
     c128 *x, *r;             // FP64 iterate and residual, padded (doff * CT)
     c64 *r32, *y, *z;        // FP32 residual, forward and backward solutions
-    double *rn, *fn, *rprev; // per tile row ||r||^2; per block ||F||^2; [2][nb] ||r||^2 by sweep parity
+    double* rn;              // per tile row ||r||^2
     int* done;               // per block
     unsigned *fflag, *bflag; // per tile row: sweep + 1 once y (forward) / z (backward) is written
     unsigned* bar;           // grid-barrier words
@@ -346,6 +348,8 @@ struct RefShared {
     c128 xs[2][CT];       // x of the column tile and of the row tile
     c64 v[CT];            // wavefront vector
     c64 w4[4][CT];        // column-group partials of the wavefront
+    double rprev[MAXB];   // ||r||^2 of the previous sweep per block (the same in every CTA)
+    double fn[MAXB];      // ||F||^2 per block
     int act[MAXB];        // active blocks (table order, T descending)
     int lvl[CHOL_MAXT + 1];  // prefix over tile-row levels of the active blocks
     double shd[32];
@@ -495,10 +499,10 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
         const long long len = (long long)blk.T * CT;
         for (long long e = blockIdx.x * (long long)CP + t; e < len; e += (long long)gridDim.x * CP)
             B.x[blk.doff * CT + e] = mk<double>(0.0, 0.0);
-        if (blockIdx.x == 0 && t == 0) {
-            B.done[bi] = B.flags[bi] != 0 ? 1 : 0;
-            B.rprev[bi] = 0.0;
-            B.rprev[nb + bi] = 0.0;
+        if (blockIdx.x == 0 && t == 0) B.done[bi] = B.flags[bi] != 0 ? 1 : 0;
+        if (t == 0) {
+            sm.rprev[bi] = 0.0;
+            sm.fn[bi] = 0.0;
         }
     }
     if (!chol_grid_sync(B.bar, status, &sm.ok, wait_ns)) return;
@@ -568,7 +572,8 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
             for (int i = t & 31; i < blk.T; i += 32) s += __ldcg(&B.rn[blk.doff + i]);
             s = warp_sum(s);
             if ((t & 31) == 0) {
-                const double fn = it == 0 ? s : __ldcg(&B.fn[bi]);
+                if (it == 0) sm.fn[bi] = s;
+                const double fn = sm.fn[bi], prev = sm.rprev[bi];
                 bool fin = false;
                 int fl = 0;
                 if (!isfinite(s)) {
@@ -576,19 +581,18 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
                     fl = CF_NONFINITE;
                 } else if (s <= CHOL_TOL * CHOL_TOL * fn) {
                     fin = true;
-                } else if (it >= 2 && s > __ldcg(&B.rprev[((it - 1) & 1) * nb + bi])) {
+                } else if (it >= 1 && s <= CHOL_FLOOR * CHOL_FLOOR * fn && s > 0.0625 * prev) {
+                    fin = true;  // at the residual's rounding floor: no further sweep helps
+                } else if (it >= 2 && s > prev) {
                     fin = true;  // diverging: the FP32 factor is too far from S~ for this block
                     fl = CF_CONV;
                 } else if (it == maxit - 1) {
                     fin = true;
                     fl = CF_CONV;
                 }
+                sm.rprev[bi] = s;
                 sm.act[a] = fin ? -1 - bi : bi;  // marked for this CTA; written back below
-                if (blockIdx.x == 0) {
-                    if (it == 0) B.fn[bi] = s;
-                    B.rprev[(it & 1) * nb + bi] = s;  // read by every CTA in the next sweep
-                    if (fl) atomicOr(&B.flags[bi], fl);
-                }
+                if (blockIdx.x == 0 && fl) atomicOr(&B.flags[bi], fl);
             }
         }
         __syncthreads();
@@ -730,7 +734,7 @@ __global__ void chol_out_kernel(CBufs B, int nb, double eta, c128* __restrict__ 
 
 // ------------------------------------------------------------------ host side
 struct CLayout {
-    size_t tab, pref, L, Dinv, fro, flags, P, x, r, r32, y, z, rn, fn, rprev, done, fflag, bflag, bar, total;
+    size_t tab, pref, L, Dinv, fro, flags, P, x, r, r32, y, z, rn, done, fflag, bflag, bar, total;
 };
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -794,8 +798,6 @@ CLayout chol_layout(const CTab& tab) {
     L.y = take(8ull * CT * rows);
     L.z = take(8ull * CT * rows);
     L.rn = take(8ull * rows);
-    L.fn = take(8ull * nb);
-    L.rprev = take(8ull * 2 * nb);
     L.done = take(4ull * nb);
     L.fflag = take(4ull * rows);
     L.bflag = take(4ull * rows);
@@ -851,8 +853,6 @@ int launch_chol_solve(const c128* S, const int64_t* block_off, int nb, const c12
     B.y = reinterpret_cast<c64*>(W + L.y);
     B.z = reinterpret_cast<c64*>(W + L.z);
     B.rn = reinterpret_cast<double*>(W + L.rn);
-    B.fn = reinterpret_cast<double*>(W + L.fn);
-    B.rprev = reinterpret_cast<double*>(W + L.rprev);
     B.done = reinterpret_cast<int*>(W + L.done);
     B.fflag = reinterpret_cast<unsigned*>(W + L.fflag);
     B.bflag = reinterpret_cast<unsigned*>(W + L.bflag);

@@ -288,7 +288,7 @@ __global__ void ldl_solve_kernel(SolveBufs B, int nb, double shift, DevStatus* s
 __global__ void __launch_bounds__(512) ql_solve_kernel(SolveBufs B, int nb, SolveArgs a, DevStatus* status) {
     extern __shared__ __align__(16) double qsm[];
     const EBlk blk = B.tab[blockIdx.x];
-    if (B.info[blockIdx.x].n_dropped == 0) return;
+    if (B.info[blockIdx.x].n_dropped == 0 && !a.want_vectors) return;
     const int n = blk.n;
     double* rc = qsm;          // cosines [n]
     double* rs = qsm + n;      // sines   [n]
@@ -807,6 +807,96 @@ static int solve_fp64(SolveBufs& B, const EBTab& tab, int nmax, const c128* F, c
     }
     count_launch();
     back_kernel<<<nb, 512, 0, st>>>(B, nb, a.eta, dtheta, n_kept, status);
+    return cudaGetLastError() == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
+}
+
+// U[i][:] = Q z_i for every tridiagonal eigenvector z_i (row i of the QL's Zt) of block 0:
+// the reflectors H_k = I - tau_k v_k v_k^H applied for k = n-2 .. 0 (eigenvector-major output).
+__global__ void __launch_bounds__(256) eigvec_back_kernel(SolveBufs B, c128* __restrict__ U) {
+    __shared__ double sh[32];
+    const EBlk blk = B.tab[0];
+    const int n = blk.n;
+    const c128* A = B.S + blk.soff;
+    const double* zt = B.zmat + blk.soff + (long long)blockIdx.x * n;
+    c128* u = U + (long long)blockIdx.x * n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) u[r] = mk<double>(zt[r], 0.0);
+    __syncthreads();
+    for (int k = n - 2; k >= 0; --k) {
+        const c128 tau = B.tau[blk.off + k];
+        if (tau.re == 0.0 && tau.im == 0.0) continue;
+        const c128* v = A + (long long)k * n;  // v[r] for r >= k+1
+        c128 dot = mk<double>(0.0, 0.0);
+        for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) cmacc(dot, v[r], u[r]);
+        dot.re = block_sum(dot.re, sh);
+        dot.im = block_sum(dot.im, sh);
+        const c128 g = tau * dot;
+        for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) u[r] = u[r] - g * v[r];
+        __syncthreads();
+    }
+}
+
+__global__ void zero_c128_kernel(c128* __restrict__ p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = mk<double>(0.0, 0.0);
+}
+
+size_t eig_vectors_workspace_bytes(long long n) {
+    const int64_t off[2] = {0, n};
+    return solve_workspace_bytes(off, 1) + 2 * al(16ull * n);
+}
+
+int launch_eig_vectors(c128* S, long long n, double shift, double* sig, double* evals_asc, c128* U, void* work,
+                       size_t work_bytes, DevStatus* status, cudaStream_t st) {
+    if (n < 1 || n > QL_MAXN) return NQS_ERR_UNSUPPORTED;
+    const int64_t off[2] = {0, n};
+    const SolveLayoutAll LA = layout_all(off, 1);
+    if (work_bytes < eig_vectors_workspace_bytes(n)) return NQS_ERR_WORKSPACE;
+    char* W = static_cast<char*>(work);
+    c128* F0 = reinterpret_cast<c128*>(W + LA.total);
+    c128* dth = reinterpret_cast<c128*>(W + LA.total + al(16ull * n));
+    count_launch();
+    zero_c128_kernel<<<64, 256, 0, st>>>(F0, n);
+    SolveArgs a{};
+    a.shift = shift;
+    a.cutoff = 0.0;  // every eigenvalue kept here: the diagnostics apply their own cutoff
+    a.eta = 1.0;
+    a.cutoff_mode = 0;
+    a.want_evals = true;
+    a.ql_maxit = limits().ql_maxit;
+    a.want_vectors = true;
+    Built bt;
+    build_table(off, 1, &bt);
+    SolveBufs B;
+    const SolveLayout& L = LA.L;
+    B.tab = reinterpret_cast<EBlk*>(W + L.tab);
+    B.S = S;
+    B.d = reinterpret_cast<double*>(W + L.d);
+    B.e = reinterpret_cast<double*>(W + L.e);
+    B.e2 = reinterpret_cast<double*>(W + L.e2);
+    B.ev = reinterpret_cast<double*>(W + L.ev);
+    B.tau = reinterpret_cast<c128*>(W + L.tau);
+    B.f = reinterpret_cast<c128*>(W + L.f);
+    B.v0 = reinterpret_cast<c128*>(W + L.v0);
+    B.v1 = reinterpret_cast<c128*>(W + L.v1);
+    B.w = reinterpret_cast<c128*>(W + L.w);
+    B.x = reinterpret_cast<c128*>(W + L.x);
+    B.z = reinterpret_cast<c128*>(W + L.z);
+    B.info = reinterpret_cast<BlkInfo*>(W + L.info);
+    B.bcol = reinterpret_cast<c128*>(W + L.bcol);
+    B.pvf = reinterpret_cast<c128*>(W + L.pvf);
+    B.pxv = reinterpret_cast<c128*>(W + L.pxv);
+    B.ypart = reinterpret_cast<c128*>(W + L.ypart);
+    B.zmat = reinterpret_cast<double*>(W + L.zmat);
+    B.bar = reinterpret_cast<unsigned*>(W + LA.bar);
+    count_launch();
+    upload_tab_kernel<<<1, 256, 0, st>>>(bt.tab, const_cast<EBlk*>(B.tab));
+    if (cudaGetLastError() != cudaSuccess) return NQS_ERR_CUDA;
+    int rc = solve_fp64(B, bt.tab, bt.nmax, F0, a, dth, evals_asc, nullptr, n, status, st);
+    if (rc) return rc;
+    count_launch();
+    eigvec_back_kernel<<<(unsigned)n, 256, 0, st>>>(B, U);
+    if (cudaMemcpyAsync(sig, B.ev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return NQS_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? NQS_OK : NQS_ERR_CUDA;
 }
 

@@ -58,6 +58,7 @@ template <typename R> struct TrdBufs {
 
 constexpr int QNB = 32;      // reflectors per panel of the blocked (WY) application of Q
 constexpr double REF_TOL = 1e-14;
+constexpr double REF_FLOOR = 1e-12;  // accepted once the residual stops contracting (rounding floor)
 
 struct MixBufs {
     const EBlk* tab;

@@ -591,6 +591,7 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
     __shared__ int sn[MAXB];
     __shared__ long long cbase[MAXB + 1];  // prefix of row chunks over slots (pdot rows)
     __shared__ int sdone[MAXB];
+    __shared__ double sprev[MAXB];  // ||r||^2 of the previous sweep (the same in every CTA)
     __shared__ long long pref[MAXB + 1];
     __shared__ long long wsum[PT / 32];
     __shared__ double shd[32];
@@ -626,7 +627,10 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
         if (tid == 0) M.fn[b] = s;
     }
     if (!grid_sync(bar, status, W_SOLVE, &ok_s, wait_ns)) return;
-    for (int b = tid; b < nb; b += PT) sdone[b] = (M.fn[b] == 0.0) ? 1 : 0;
+    for (int b = tid; b < nb; b += PT) {
+        sdone[b] = (M.fn[b] == 0.0) ? 1 : 0;
+        sprev[b] = 0.0;
+    }
     __syncthreads();
 
     for (int it = 0; it < maxit; ++it) {
@@ -770,8 +774,13 @@ __global__ void __launch_bounds__(PT, 2) refine_persist_kernel(SolveBufs B, MixB
             s = warp_sum(s);
             if ((tid & 31) == 0) {
                 // a block that does not converge (or turns non-finite) keeps done = 0: the host
-                // then solves every block by the FP64 path (under capture: NQS_ERR_RETRY)
-                if (s <= REF_TOL * REF_TOL * M.fn[b]) sdone[b] = 1;
+                // then solves every block by the FP64 path (under capture: NQS_ERR_RETRY).
+                // Below REF_FLOOR ||F|| a residual that has stopped contracting is at the FP64
+                // residual's rounding floor and is accepted.
+                if (s <= REF_TOL * REF_TOL * M.fn[b] ||
+                    (it >= 1 && s <= REF_FLOOR * REF_FLOOR * M.fn[b] && s > 0.0625 * sprev[b]))
+                    sdone[b] = 1;
+                sprev[b] = s;
             }
         }
         __syncthreads();

@@ -148,8 +148,22 @@ struct SolveArgs {
     cudaEvent_t ev_trd_start;   // recorded just before the tridiagonal reduction (or NULL)
     bool no_host_sync;          // capturable: the mixed certificate is checked on the device
     int ql_maxit;               // implicit-QL sweep limit per eigenvalue
+    bool want_vectors;          // FP64 path: form every block's tridiagonal eigenvectors (QL)
 };
 size_t solve_workspace_bytes(const int64_t* block_off, int nb);
+// Full FP64 eigen-decomposition of one n x n Hermitian matrix S (lower triangle used;
+// OVERWRITTEN with reflectors): S + shift I = U diag(sig) U^H. sig[i] (unsorted) pairs with
+// the eigenvector U[i*n .. i*n+n) (eigenvector-major); evals_asc gets the eigenvalues ascending.
+size_t eig_vectors_workspace_bytes(long long n);
+int launch_eig_vectors(c128* S, long long n, double shift, double* sig, double* evals_asc, c128* U, void* work,
+                       size_t work_bytes, DevStatus* status, cudaStream_t st);
+// Inverse-metric diagnostics (Eq. 4) from two eigen-decompositions (diagnostics.cu)
+cudaError_t launch_born_weights(const c128* logpsi, long long n, double* w, cudaStream_t st);
+cudaError_t launch_block_restrict(const c128* S, long long n, const int64_t* block_off, int nb, c128* out,
+                                  long long* blk_of, cudaStream_t st);
+cudaError_t launch_inverse_diagnostics(long long n, const double* sig_a, const double* ev_a, const c128* Ua,
+                                       const double* sig_b, const double* ev_b, const c128* Ub, double cutoff,
+                                       int mode, double* partial, double* out, cudaStream_t st);
 int launch_block_solve(c128* S, const int64_t* block_off, int nb, const c128* F,
                        const SolveArgs& a, c128* dtheta, double* evals, int32_t* n_kept,
                        void* work, size_t work_bytes, DevStatus* status, cudaStream_t st);
