@@ -348,6 +348,7 @@ struct RefShared {
     c128 xs[2][CT];       // x of the column tile and of the row tile
     c64 v[CT];            // wavefront vector
     c64 w4[4][CT];        // column-group partials of the wavefront
+    __align__(16) c64 dk[CTE];  // the unit's diagonal-tile inverse
     double rprev[MAXB];   // ||r||^2 of the previous sweep per block (the same in every CTA)
     double fn[MAXB];      // ||F||^2 per block
     int act[MAXB];        // active blocks (table order, T descending)
@@ -409,10 +410,26 @@ __device__ bool wait_flag(const unsigned* flag, unsigned want, DevStatus* status
     return *ok_s != 0;
 }
 
+// Every thread's writes of the part are ordered before the flag: barrier, then one
+// thread's device-wide fence and the flag update.
 __device__ __forceinline__ void publish_flag(unsigned* flag, unsigned v) {
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicMax(flag, v);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicMax(flag, v);
+    }
+}
+
+// Whether flag >= want now (thread 0 reads once; acquire fence when set); no waiting.
+__device__ bool peek_flag(const unsigned* flag, unsigned want, int* ok_s) {
+    if (threadIdx.x == 0) {
+        const volatile unsigned* f = flag;
+        const int ok = *f >= want ? 1 : 0;
+        if (ok) __threadfence();
+        *ok_s = ok;
+    }
+    __syncthreads();
+    return *ok_s != 0;
 }
 
 __device__ __forceinline__ c64 ldcg64(const c64* p) {
@@ -622,7 +639,11 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
         __syncthreads();
         const long long U = sm.lvl[Tm];
         const unsigned gen = (unsigned)it + 1u;
-        // ---- P4: forward (units 0..U-1, tile rows ascending) then backward (U..2U-1, descending)
+        // ---- P4: forward (units 0..U-1, tile rows ascending) then backward (U..2U-1, descending).
+        // A unit applies its off-diagonal tiles in the order their right-hand parts become
+        // ready (forward: j = 0 .. i-1; backward: j = T-1 .. i+1), loading each tile before it
+        // waits for the part it multiplies, and skips the waits once a later part is known to
+        // be ready (a part is published only after every part it depends on).
         for (long long u = blockIdx.x; u < 2 * U; u += gridDim.x) {
             const bool fwd = u < U;
             const long long v = fwd ? u : u - U;
@@ -637,19 +658,32 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
             const CBlk blk = B.tab[bi];
             const int ti = fwd ? lev : blk.T - 1 - lev;
             const long long row0 = blk.doff;  // tile-row base of the block
-            const c64* Dk = B.Dinv + (blk.doff + ti) * CTE;
+            {   // the diagonal tile's inverse to shared memory (needed last)
+                const float4* src = reinterpret_cast<const float4*>(B.Dinv + (blk.doff + ti) * CTE);
+                float4* dst = reinterpret_cast<float4*>(sm.dk);
+                for (int e = t; e < CTE / 2; e += CP) dst[e] = src[e];
+            }
             if (fwd) {
                 // v = r_i - sum_{j < i} L_ij y_j ; y_i = Dinv_i v
                 const int r = t >> 2, q = t & 3;
                 float ar = 0.f, ai = 0.f;
+                int known = -1;  // flags 0..known acquired
+                if (ti > 0 && peek_flag(B.fflag + row0 + ti - 1, gen, &sm.ok)) known = ti - 1;
                 for (int j = 0; j < ti; ++j) {
-                    if (!wait_flag(B.fflag + row0 + j, gen, status, &sm.ok, wait_ns)) return;
-                    const c64* Lt = B.L + tile_at(blk, ti, j) * CTE + r * CT;
-                    const c64* yj = B.y + (row0 + j) * CT;
-                    for (int c = q; c < CT; c += 4) {
-                        const c64 a = Lt[c], yv = ldcg64(yj + c);
-                        ar = fmaf(a.re, yv.re, fmaf(-a.im, yv.im, ar));
-                        ai = fmaf(a.re, yv.im, fmaf(a.im, yv.re, ai));
+                    const c64* Lt = B.L + tile_at(blk, ti, j) * CTE + r * CT + q;
+                    c64 a[CT / 4];
+#pragma unroll
+                    for (int m = 0; m < CT / 4; ++m) a[m] = Lt[4 * m];
+                    if (j > known) {
+                        if (!wait_flag(B.fflag + row0 + j, gen, status, &sm.ok, wait_ns)) return;
+                        known = j;
+                    }
+                    const c64* yj = B.y + (row0 + j) * CT + q;
+#pragma unroll
+                    for (int m = 0; m < CT / 4; ++m) {
+                        const c64 yv = ldcg64(yj + 4 * m);
+                        ar = fmaf(a[m].re, yv.re, fmaf(-a[m].im, yv.im, ar));
+                        ai = fmaf(a[m].re, yv.im, fmaf(a[m].im, yv.re, ai));
                     }
                 }
                 ar += __shfl_xor_sync(0xffffffffu, ar, 1);
@@ -663,7 +697,7 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
                 __syncthreads();
                 float yr = 0.f, yi = 0.f;
                 for (int c = q; c < CT; c += 4) {
-                    const c64 a = Dk[r * CT + c], vv = sm.v[c];
+                    const c64 a = sm.dk[r * CT + c], vv = sm.v[c];
                     yr = fmaf(a.re, vv.re, fmaf(-a.im, vv.im, yr));
                     yi = fmaf(a.re, vv.im, fmaf(a.im, vv.re, yi));
                 }
@@ -677,14 +711,23 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
                 // w = y_i - sum_{j > i} L_ji^H z_j ; z_i = Dinv_i^H w ; x_i += z_i
                 const int c = t & (CT - 1), g = t >> 6;
                 float ar = 0.f, ai = 0.f;
-                for (int j = ti + 1; j < blk.T; ++j) {
-                    if (!wait_flag(B.bflag + row0 + j, gen, status, &sm.ok, wait_ns)) return;
-                    const c64* Lt = B.L + tile_at(blk, j, ti) * CTE;
-                    const c64* zj = B.z + (row0 + j) * CT;
-                    for (int rr = g * 16; rr < g * 16 + 16; ++rr) {
-                        const c64 a = Lt[rr * CT + c], zv = ldcg64(zj + rr);  // conj(a) z
-                        ar = fmaf(a.re, zv.re, fmaf(a.im, zv.im, ar));
-                        ai = fmaf(a.re, zv.im, fmaf(-a.im, zv.re, ai));
+                int known = blk.T;  // flags known .. T-1 acquired
+                if (ti + 1 < blk.T && peek_flag(B.bflag + row0 + ti + 1, gen, &sm.ok)) known = ti + 1;
+                for (int j = blk.T - 1; j > ti; --j) {
+                    const c64* Lt = B.L + tile_at(blk, j, ti) * CTE + (g * 16) * CT + c;
+                    c64 a[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) a[m] = Lt[m * CT];
+                    if (j < known) {
+                        if (!wait_flag(B.bflag + row0 + j, gen, status, &sm.ok, wait_ns)) return;
+                        known = j;
+                    }
+                    const c64* zj = B.z + (row0 + j) * CT + g * 16;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        const c64 zv = ldcg64(zj + m);  // conj(a) z
+                        ar = fmaf(a[m].re, zv.re, fmaf(a[m].im, zv.im, ar));
+                        ai = fmaf(a[m].re, zv.im, fmaf(-a[m].im, zv.re, ai));
                     }
                 }
                 if (!wait_flag(B.fflag + row0 + ti, gen, status, &sm.ok, wait_ns)) return;
@@ -698,7 +741,7 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
                 __syncthreads();
                 float zr = 0.f, zi = 0.f;
                 for (int rr = g * 16; rr < g * 16 + 16; ++rr) {
-                    const c64 a = Dk[rr * CT + c], vv = sm.v[rr];  // conj(Dinv[rr][c]) w[rr]
+                    const c64 a = sm.dk[rr * CT + c], vv = sm.v[rr];  // conj(Dinv[rr][c]) w[rr]
                     zr = fmaf(a.re, vv.re, fmaf(a.im, vv.im, zr));
                     zi = fmaf(a.re, vv.im, fmaf(-a.im, vv.re, zi));
                 }
