@@ -388,6 +388,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     theta = torch.as_tensor(w.theta, device="cuda")
     x = torch.as_tensor(w.configs, device="cuda")
     ham = nq.Hamiltonian(w.model.n_sites, w.bond_ij, w.bond_j, w.c, w.sign_rule)
+    # tile order of the tensor-core Gram: timed on this GPU by the project's tuner for this shape
+    gram_tuning = None
+    if w.precision.startswith("split"):
+        from paper_2510_08430_gb300 import tune
+        rec = tune.tune([([int(v) for v in np.diff(w.block_off)], w.n_samples)], precision=w.precision,
+                        cache_path=None)
+        key = tune.bucket(int(np.diff(w.block_off).max()), w.n_samples)
+        gram_tuning = {"group": rec[key]["group"], "candidates_ms": rec[key]["ms"],
+                       "what": "edge G of the square groups of 128x128 tiles the persistent Gram takes in turn"}
     step = nq.SRStep(model, w.n_samples, ham, w.block_off, w.precision, w.diag_shift, w.cutoff, solver=args.solver,
                      param_space=args.param_space)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -500,6 +509,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
         "config": dict(workload_desc(w, args.solver), parallelism=("replicas" if world > 1 else "single")),
         "stage_ms": st_mean,
+        "gram_tuning": gram_tuning,
         "dtheta_within_tol": acc["within"],
         "accuracy": acc,
         "roofline": dict(roof, dominant_stage=dominant),

@@ -424,6 +424,19 @@ NQS_API int qgt_inverse_diagnostics(const void* S_a, const int64_t* block_off_a,
  * default. Results computed under lowered limits are not the definition's. */
 NQS_API int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns);
 
+/* ---- tuning of the tensor-core Gram ----
+ * The persistent tcgen05 Gram takes the 128 x 128 tiles of each block in square groups of
+ * G x G tiles, so that the CTAs running at the same time share G row and G column panels
+ * in L2. nqs_set_gram_tuning installs a table (process-wide, at most 64 entries; n = 0
+ * clears it): a call whose largest block has at most max_nb[e] parameters and which sums
+ * at most max_ns[e] samples uses group[e] (1 <= group <= 64), the first matching entry
+ * wins; without a match G = 8. The table is written by the project's tuner
+ * (paper_2510_08430_gb300.tune), which times the candidates on the device. The choice changes
+ * only the order of the tiles, never the arithmetic: S is bitwise the same for every G.
+ * nqs_gram_group_edge returns the G a call with that shape would use. */
+NQS_API int nqs_set_gram_tuning(int32_t n, const int64_t* max_nb, const int64_t* max_ns, const int32_t* group);
+NQS_API int32_t nqs_gram_group_edge(int64_t max_nb, int64_t n_s);
+
 NQS_API int nqs_stage_timing(nqs_workspace* ws, int32_t enable);
 NQS_API int nqs_stage_times(nqs_workspace* ws, double* ms_out, int32_t max_stages, int32_t* n_stages);
 NQS_API int64_t nqs_launch_count(void);

@@ -80,6 +80,8 @@ SIGNATURES = {
     "nqs_launch_count": (C.c_int64, []),
     "nqs_set_limits": (C.c_int, [I32, I64]),
     "nqs_born_weights": (C.c_int, [P, I64, P, P]),
+    "nqs_set_gram_tuning": (C.c_int, [I32, OFF, OFF, C.POINTER(C.c_int32)]),
+    "nqs_gram_group_edge": (C.c_int32, [I64, I64]),
     "qgt_inverse_diagnostics_workspace_size": (C.c_int, [I64, SZ]),
     "qgt_inverse_diagnostics": (C.c_int, [P, OFF, I32, P, I64, D, D, I32, P, P, P]),
 }

@@ -7,6 +7,7 @@
 #include <string>
 #include <new>
 #include <atomic>
+#include <mutex>
 #include <cuda_bf16.h>
 #include "internal.cuh"
 #include "eigh.cuh"
@@ -35,6 +36,24 @@ std::atomic<int> g_ql_maxit{QL_MAXIT_DEFAULT};
 std::atomic<int> g_ref_maxit{REF_MAXIT_DEFAULT};
 std::atomic<unsigned long long> g_wait_ns{WAIT_NS_DEFAULT};
 }  // namespace
+
+namespace {
+constexpr int GRAM_TUNE_MAX = 64;
+struct GramTune {
+    long long max_nb, max_ns;
+    int group;
+};
+std::mutex g_tune_mu;
+int g_tune_n = 0;
+GramTune g_tune[GRAM_TUNE_MAX];
+}  // namespace
+
+int nqs::gram_group_edge(long long max_nb, long long ns) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int i = 0; i < g_tune_n; ++i)
+        if (max_nb <= g_tune[i].max_nb && ns <= g_tune[i].max_ns) return g_tune[i].group;
+    return GRAM_GROUP_EDGE_DEFAULT;
+}
 
 nqs::Limits nqs::limits() {
     return Limits{g_ql_maxit.load(std::memory_order_relaxed), g_ref_maxit.load(std::memory_order_relaxed),
@@ -580,6 +599,21 @@ int nqs_stage_times(nqs_workspace* ws, double* ms_out, int32_t max_stages, int32
     *n_stages = n;
     return NQS_OK;
 }
+
+int nqs_set_gram_tuning(int32_t n, const int64_t* max_nb, const int64_t* max_ns, const int32_t* group) {
+    if (n < 0 || n > GRAM_TUNE_MAX || (n > 0 && (!max_nb || !max_ns || !group)))
+        return fail(NQS_ERR_INVALID_ARG, "nqs_set_gram_tuning: 0 <= n <= %d entries with non-NULL arrays",
+                    GRAM_TUNE_MAX);
+    for (int i = 0; i < n; ++i)
+        if (group[i] < 1 || group[i] > 64 || max_nb[i] < 1 || max_ns[i] < 1)
+            return fail(NQS_ERR_INVALID_ARG, "nqs_set_gram_tuning: entry %d out of range", i);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_n = n;
+    for (int i = 0; i < n; ++i) g_tune[i] = GramTune{max_nb[i], max_ns[i], group[i]};
+    return NQS_OK;
+}
+
+int32_t nqs_gram_group_edge(int64_t max_nb, int64_t n_s) { return gram_group_edge(max_nb, n_s); }
 
 int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns) {
     if (max_sweeps < 0 || wait_ns < 0) return fail(NQS_ERR_INVALID_ARG, "nqs_set_limits: negative limit");

@@ -15,6 +15,7 @@ constexpr int GK = 16;   // samples per shared-memory stage
 
 void gram_table(const int64_t* block_off, int nb, int tile_rows, GramTable* tab) {
     tab->nb = nb;
+    tab->group = 1;
     long long tiles = 0, soff = 0;
     for (int b = 0; b < nb; ++b) {
         const long long n = block_off[b + 1] - block_off[b];

@@ -24,6 +24,7 @@
 // NQS_ERR_TIMEOUT, drains its own copies and MMAs, frees tensor memory and
 // returns.
 #include <cstdlib>
+#include <new>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include "internal.cuh"
@@ -196,6 +197,19 @@ struct TileInfo {
     int b, I, J;
 };
 
+__device__ __forceinline__ void tri_decode(long long r, long long* I, long long* J) {
+    long long i = (long long)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= r) ++i;
+    while (i * (i + 1) / 2 > r) --i;
+    *I = i;
+    *J = r - i * (i + 1) / 2;
+}
+
+// Tile t of the launch -> (block, I, J), J <= I. Within a block the lower-triangle tiles are
+// taken in square groups of G x G (G = tab.group): super-rows of G tile rows in turn; in each,
+// the off-diagonal G x G groups left to right (row-major inside), then the diagonal group's
+// lower triangle. Consecutive tiles (the CTAs running at the same time) then share G row panels
+// and G column panels, which stay in L2 while they stream the samples. G = 1 is row by row.
 __device__ __forceinline__ TileInfo decode(const GramTable& tab, long long t) {
     int lo = 0, hi = tab.nb - 1;
     while (lo < hi) {
@@ -203,13 +217,32 @@ __device__ __forceinline__ TileInfo decode(const GramTable& tab, long long t) {
         if (tab.b[mid].tile0 <= t) lo = mid; else hi = mid - 1;
     }
     const long long r = t - tab.b[lo].tile0;
-    long long i = (long long)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
-    while ((i + 1) * (i + 2) / 2 <= r) ++i;
-    while (i * (i + 1) / 2 > r) --i;
+    const long long G = tab.group > 0 ? tab.group : 1;
+    const long long T = (tab.b[lo].n + BM / 2 - 1) / (BM / 2);  // tile rows of the block
+    // super-row S (rows S G .. S G + h - 1, h = min(G, T - S G)) holds h S G + h (h + 1) / 2 tiles;
+    // every super-row before the last has h = G
+    long long Sr = 0, base = 0;
+    for (;;) {
+        const long long h = (T - Sr * G) < G ? (T - Sr * G) : G;
+        const long long cnt = h * Sr * G + h * (h + 1) / 2;
+        if (r < base + cnt || h < G) break;  // the last super-row has h <= G
+        base += cnt;
+        ++Sr;
+    }
+    const long long h = (T - Sr * G) < G ? (T - Sr * G) : G;
+    const long long u = r - base;
     TileInfo ti;
     ti.b = lo;
-    ti.I = (int)i;
-    ti.J = (int)(r - i * (i + 1) / 2);
+    if (u < h * Sr * G) {       // off-diagonal group J' = u / (h G), row-major inside
+        const long long Jg = u / (h * G), loc = u % (h * G);
+        ti.I = (int)(Sr * G + loc / G);
+        ti.J = (int)(Jg * G + loc % G);
+    } else {                    // diagonal group: lower triangle of h x h
+        long long i, j;
+        tri_decode(u - h * Sr * G, &i, &j);
+        ti.I = (int)(Sr * G + i);
+        ti.J = (int)(Sr * G + j);
+    }
     return ti;
 }
 
@@ -486,6 +519,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 }  // namespace tc
 
+cudaError_t launch_gram_tc_tab(int nsplit, const void* const* planes, const int8_t* gexp, long long np,
+                               long long rows, long long ldk, long long kpad, double scale, const GramTable& tab,
+                               c128* S, DevStatus* status, cudaStream_t st);
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -531,8 +568,22 @@ static cudaError_t launch_tc(const tc::Maps& maps, const GramTable& tab, long lo
 }
 
 cudaError_t launch_gram_tc(int nsplit, const void* const* planes, const int8_t* gexp, long long np, long long rows,
-                           long long ldk, long long kpad, double scale, const GramTable& tab, c128* S,
+                           long long ldk, long long kpad, double scale, const GramTable& tab_in, c128* S,
                            DevStatus* status, cudaStream_t st) {
+    // the tile-group edge of this call from the tuning table (largest block, samples summed)
+    GramTable* tabp = new (std::nothrow) GramTable(tab_in);
+    if (!tabp) return cudaErrorMemoryAllocation;
+    long long max_nb = 0;
+    for (int b = 0; b < tabp->nb; ++b) max_nb = tabp->b[b].n > max_nb ? tabp->b[b].n : max_nb;
+    tabp->group = gram_group_edge(max_nb, kpad);
+    const cudaError_t e = launch_gram_tc_tab(nsplit, planes, gexp, np, rows, ldk, kpad, scale, *tabp, S, status, st);
+    delete tabp;
+    return e;
+}
+
+cudaError_t launch_gram_tc_tab(int nsplit, const void* const* planes, const int8_t* gexp, long long np,
+                               long long rows, long long ldk, long long kpad, double scale, const GramTable& tab,
+                               c128* S, DevStatus* status, cudaStream_t st) {
     static int kpi = -1;  // MMA K-steps per accumulator flush (1, 2 or 4); NQS_GRAM_KPI overrides
     if (kpi < 0) {
         const char* env = getenv("NQS_GRAM_KPI");

@@ -109,9 +109,15 @@ struct GBlk {                   // one QGT block of one instance
 };
 struct GramTable {
     int nb;
+    int group;                  // tensor-core Gram: edge of the square groups of tiles taken in turn (1: by rows)
     long long total_tiles;
     GBlk b[MAXB];
 };
+// Tile-group edge of the tensor-core Gram for a call whose largest block has max_nb parameters
+// and which sums ns samples: the tuning table's first matching entry (nqs_set_gram_tuning),
+// else GRAM_GROUP_EDGE_DEFAULT.
+constexpr int GRAM_GROUP_EDGE_DEFAULT = 8;
+int gram_group_edge(long long max_nb, long long ns);
 cudaError_t launch_gram_simt(int prec, const void* dO, long long ldo, long long ns, const double* w,
                              double scale, const GramTable& tab, c128* S, cudaStream_t st);
 constexpr int GRAM_KPI_DEFAULT = 4;    // MMA K-steps (16 samples) per accumulator flush
