@@ -73,14 +73,23 @@ extern "C" {
  * NQS_SPLIT_BF16X3: as NQS_SPLIT_BF16 with hi + mid + lo and six products
  *                   (all terms above 2^-16 relative): representation error 2^-25.
  * NQS_SPLIT_BF16_EXACT: error-free split on the tensor cores: for every parameter and
- *                   every group of 16 samples the centred values are scaled by a common
+ *                   every group of 32 samples the centred values are scaled by a common
  *                   power of two and split into five BF16 slices holding integers of at
  *                   most 8 bits, so that the MMA sums of the leading products are exact;
  *                   fifteen products (every term above 2^-32 of the group scale) per group,
  *                   groups summed in double-float. Better than FP32 rounding of the data
  *                   even on heavy-tailed Jacobian rows.
- * Local energies in the split modes are those of NQS_FP64. The per-block shifted
- * eigen-decomposition and solve is selected separately (solver argument, below). */
+ * Local energies in the split modes: RBMs and one-layer networks as in NQS_FP64; FFNNs by
+ * FP32 difference propagation: for every connected configuration x' the changes of the
+ * pre-activations dz and of the hidden units dh = lncosh(z + dz) - lncosh(z) =
+ * log1p(2 sinh(dz/2) (sinh(dz/2) + cosh(dz/2) tanh z)) relative to the parent sample x
+ * (z and tanh z from its FP64 forward) are carried through the layers in FP32, following
+ * the ln cosh branch of the exact forward, so that ln psi(x') - ln psi(x) carries FP32
+ * rounding of the differences only (about 1e-7 relative on E_loc); the rare connections
+ * whose branch or range FP32 cannot decide are recomputed in the NQS_FP64 arithmetic.
+ * The sr_step flag NQS_ELOC_FP64 selects the NQS_FP64 local energies instead.
+ * The per-block shifted eigen-decomposition and solve is selected separately (solver
+ * argument, below). */
 typedef enum {
     NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3, NQS_SPLIT_BF16_EXACT = 4
 } nqs_precision;
@@ -170,8 +179,9 @@ NQS_API int nqs_vjp(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_
 /* nqs_local_energy -- E_loc(x_s) (Eq. 1) for the Hamiltonian h:
  *   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign_rule psi(x^{ij})/psi(x) ],
  * x^{ij} = x with spins i and j flipped; connected configurations are visited in
- * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32; otherwise FP64, with the
- * FFNN hidden layers of the connected forwards in double-float (about 2^-46 relative). */
+ * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32; FP64 for NQS_FP64, with
+ * the FFNN hidden layers of the connected forwards in double-float (about 2^-46 relative);
+ * the split precisions as described under nqs_precision (FFNN: FP32 difference propagation). */
 NQS_API int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
                      const nqs_hamiltonian* h, int32_t precision, void* eloc_out,
                      nqs_workspace* ws, void* stream);
@@ -328,6 +338,8 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
  *   evals_out / n_kept_out as in qgt_block_solve (may be NULL).
  *   flags: NQS_SYNC makes the call synchronise and return device status.
  *          NQS_PARAM_SPACE solves every block in parameter space (see below).
+ *          NQS_ELOC_FP64 computes the local energies of the split precisions in the
+ *          FP64-class arithmetic of NQS_FP64 instead of FP32 difference propagation.
  *          NQS_GRAPH makes the call capturable into a CUDA graph (stream capture):
  *          nothing synchronises with the host. The mixed solver's certificate is then
  *          checked on the device; when it fails the step's dtheta is not the definition's
@@ -338,6 +350,7 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
 #define NQS_SYNC 1
 #define NQS_GRAPH 2
 #define NQS_PARAM_SPACE 4
+#define NQS_ELOC_FP64 8
 /* Blocks wider than the sample count. With the mixed solver, diag_shift > 0, precision
  * NQS_FP64 or NQS_SPLIT_BF16_EXACT and no NQS_PARAM_SPACE flag, a block with n_b > n_s is
  * solved in sample space (push-through identity):
@@ -423,6 +436,12 @@ NQS_API int qgt_inverse_diagnostics(const void* S_a, const int64_t* block_off_a,
  * 2 s); a wait that runs out records NQS_ERR_TIMEOUT and its kernel returns. 0 restores a
  * default. Results computed under lowered limits are not the definition's. */
 NQS_API int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns);
+
+/* nqs_set_eloc_fallback_all -- test hook (process-wide): on != 0 sends every connection of
+ * the FP32 difference-propagation local energies (split precisions, FFNN) to the FP64-class
+ * kernel that otherwise recomputes only the connections FP32 cannot follow, so that this
+ * path can be checked on its own; the results are then those of NQS_FP64. 0 restores. */
+NQS_API int nqs_set_eloc_fallback_all(int32_t on);
 
 /* ---- tuning of the tensor-core Gram ----
  * The persistent tcgen05 Gram takes the 128 x 128 tiles of each block in square groups of

@@ -25,6 +25,7 @@ NQS_RBM, NQS_FFNN = 0, 1
 NQS_SYNC = 1
 NQS_GRAPH = 2
 NQS_PARAM_SPACE = 4
+NQS_ELOC_FP64 = 8
 NQS_SOLVE_FP64, NQS_SOLVE_MIXED, NQS_SOLVE_MIXED_PSD = 0, 1, 2
 NQS_STATIC_MAX_SAMPLES = 65536
 
@@ -79,6 +80,7 @@ SIGNATURES = {
     "nqs_stage_times": (C.c_int, [P, C.POINTER(C.c_double), I32, C.POINTER(C.c_int32)]),
     "nqs_launch_count": (C.c_int64, []),
     "nqs_set_limits": (C.c_int, [I32, I64]),
+    "nqs_set_eloc_fallback_all": (C.c_int, [I32]),
     "nqs_born_weights": (C.c_int, [P, I64, P, P]),
     "nqs_set_gram_tuning": (C.c_int, [I32, OFF, OFF, C.POINTER(C.c_int32)]),
     "nqs_gram_group_edge": (C.c_int32, [I64, I64]),

@@ -14,6 +14,9 @@
 
 using namespace nqs;
 
+static std::atomic<int> g_dp_fallback_all{0};
+bool nqs::dp_fallback_all() { return g_dp_fallback_all.load() != 0; }
+
 constexpr int NSTAGE = 6;  // jacobian, local energy, centring+force, gram, tridiagonal reduction, solve
 struct nqs_workspace {
     char* base;
@@ -115,6 +118,12 @@ inline int jac_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
 // local energies: FP32 arithmetic only in NQS_FP32 mode (in the split modes an FP32
 // E_loc alone moves dtheta by ~1e-5 relative on the 10x10 workload)
 inline int eloc_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
+// split precisions: FFNN local energies by FP32 difference propagation (the FP64-class
+// double-float kernel for the connections it cannot follow) unless NQS_ELOC_FP64 is set
+inline bool eloc_dp(int prec, int flags) {
+    return (prec == NQS_SPLIT_BF16 || prec == NQS_SPLIT_BF16X3 || prec == NQS_SPLIT_BF16_EXACT) &&
+           !(flags & NQS_ELOC_FP64);
+}
 inline int nsplit_of(int prec) {
     return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : (prec == NQS_SPLIT_BF16_EXACT ? 5 : 0));
 }
@@ -171,6 +180,7 @@ struct ElocBufs {
     long long* off;
     c128* terms;
     void* wdf;  // double-float (hi, lo) copy of the transposed weights (FP64 local energies)
+    DpBufs dp;  // FP32 difference propagation (FFNN models only; null otherwise)
 };
 void plan_eloc(Arena& a, const ModelDesc& md, long long ns, int nbonds, ElocBufs* b) {
     const long long we = model_wt_elems(md);
@@ -181,6 +191,13 @@ void plan_eloc(Arena& a, const ModelDesc& md, long long ns, int nbonds, ElocBufs
     b->cbond = static_cast<int32_t*>(a.take(4 * maxc));
     b->csamp = static_cast<int32_t*>(a.take(4 * maxc));
     b->terms = static_cast<c128*>(a.take(16 * maxc));
+    b->dp = DpBufs{nullptr, nullptr, nullptr, nullptr};
+    if (dp_applicable(md)) {
+        b->dp.w32 = static_cast<float2*>(a.take(8 * (size_t)(we > 0 ? we : 1)));
+        b->dp.pz = static_cast<float4*>(a.take(16 * (size_t)model_z_elems(md, ns)));
+        b->dp.fb_list = static_cast<long long*>(a.take(8 * (size_t)(maxc > 0 ? maxc : 1)));
+        b->dp.fb_count = static_cast<unsigned long long*>(a.take(8));
+    }
 }
 
 struct BuildBufs {
@@ -210,10 +227,18 @@ int run_model(const ModelDesc& md, int prec, const void* theta, const int8_t* x,
 }
 
 int run_eloc(const ModelDesc& md, int prec, const HamDesc& hd, const int8_t* x, long long ns,
-             const JacBufs& jb, const ElocBufs& eb, c128* eloc, DevStatus* status, cudaStream_t st) {
+             const JacBufs& jb, const ElocBufs& eb, c128* eloc, DevStatus* status, cudaStream_t st,
+             bool dp = false) {
     CK(launch_conn_count(x, ns, hd, eb.cnt, status, st), "conn_count");
     CK(launch_scan(eb.cnt, ns, eb.off, st), "scan");
     CK(launch_conn_fill(x, ns, hd, eb.off, eb.cbond, eb.csamp, st), "conn_fill");
+    if (dp && prec == NQS_FP64 && eb.dp.pz) {
+        CK(launch_conn_terms_dp(md, jb.thR, jb.wtR, eb.wdf, jb.Z, jb.logpsi, x, ns, hd, eb.cbond, eb.csamp,
+                                eb.off + ns, ns * hd.n_bonds, eb.terms, eb.dp, st),
+           "conn_terms_dp");
+        CK(launch_eloc_reduce(x, ns, hd, eb.off, eb.terms, eloc, status, st), "eloc_reduce");
+        return NQS_OK;
+    }
     if (prec == NQS_FP64) CK(launch_split_weights(md, jb.wtR, eb.wdf, st), "split_weights");
     CK(launch_conn_terms(prec, md, jb.thR, jb.wtR, eb.wdf, jb.Z, jb.logpsi, x, hd, eb.cbond, eb.csamp, eb.off + ns,
                          ns * hd.n_bonds, eb.terms, st),
@@ -417,7 +442,7 @@ int run_step_wide(const ModelDesc& md, const HamDesc& hd, const void* theta, con
         rc = run_model(md, re, theta, configs, ns, w.jbe, st);
         if (rc) return rc;
     }
-    rc = run_eloc(md, re, hd, configs, ns, w.jbe, w.eb, w.eloc, status, st);
+    rc = run_eloc(md, re, hd, configs, ns, w.jbe, w.eb, w.eloc, status, st, eloc_dp(prec, flags));
     if (rc) return rc;
     if (tm) CK(cudaEventRecord(ws->ev[2], st), "event");
     CK(launch_emean(w.eloc, nullptr, ns, Emean, w.e, status, st), "emean");
@@ -623,6 +648,11 @@ int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns) {
     return NQS_OK;
 }
 
+int nqs_set_eloc_fallback_all(int32_t on) {
+    g_dp_fallback_all.store(on ? 1 : 0);
+    return NQS_OK;
+}
+
 int64_t nqs_launch_count(void) { return (int64_t)__atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); }
 
 int nqs_sync_status(nqs_workspace* ws, void* stream) {
@@ -805,7 +835,8 @@ int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* config
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
-    return run_eloc(md, rp, hd, configs, n_s, jb, eb, static_cast<c128*>(eloc_out), status_of(ws), st);
+    return run_eloc(md, rp, hd, configs, n_s, jb, eb, static_cast<c128*>(eloc_out), status_of(ws), st,
+                    eloc_dp(precision, 0));
 }
 
 int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h, int32_t* conn_count,
@@ -1062,7 +1093,7 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
         rc = run_model(md, re, theta, configs, n_s, jbe, st);
         if (rc) return rc;
     }
-    rc = run_eloc(md, re, hd, configs, n_s, jbe, eb, eloc, status, st);
+    rc = run_eloc(md, re, hd, configs, n_s, jbe, eb, eloc, status, st, eloc_dp(precision, flags));
     if (rc) return rc;
     if (tm) CK(cudaEventRecord(ws->ev[2], st), "event");
     rc = run_build(O, ldo, n_s, md.n_p, nullptr, block_off, n_blocks, eloc, precision, S, F, nullptr,
@@ -1250,7 +1281,7 @@ extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const vo
             if (err != cudaSuccess) rc = cuda_fail(err, "jacobian");
         }
         if (!rc && re != rp) rc = run_model(md, re, th, xc, ns, jbe, st);
-        if (!rc) rc = run_eloc(md, re, hd, xc, ns, jbe, eb, eloc, status, st);
+        if (!rc) rc = run_eloc(md, re, hd, xc, ns, jbe, eb, eloc, status, st, eloc_dp(precision, flags));
         if (!rc) {
             cudaError_t err = launch_emean(eloc, nullptr, ns, static_cast<c128*>(Emean_out) + i, e, status, st);
             void* pl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

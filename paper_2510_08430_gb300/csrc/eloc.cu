@@ -463,13 +463,15 @@ __global__ void __launch_bounds__(256) conn_terms_df_kernel(ModelDesc md, const 
                                                              const int8_t* __restrict__ x, HamDesc h,
                                                              const int32_t* __restrict__ cbond,
                                                              const int32_t* __restrict__ csamp,
-                                                             const long long* __restrict__ nconn_ptr, int TR,
+                                                             const long long* __restrict__ nconn_ptr,
+                                                             const long long* __restrict__ cidx, int TR,
                                                              c128* __restrict__ terms) {
+    // cidx (optional): the rows are connections cidx[0 .. *nconn_ptr) instead of 0 .. *nconn_ptr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ld = md.maxw;
-    df2* A = reinterpret_cast<df2*>(smem_raw);
-    df2* B = A + (size_t)TR * ld;
-    int* ssamp = reinterpret_cast<int*>(B + (size_t)TR * ld);
+    df2* const A0 = reinterpret_cast<df2*>(smem_raw);
+    df2* const B0 = A0 + (size_t)TR * ld;
+    int* ssamp = reinterpret_cast<int*>(B0 + (size_t)TR * ld);
     int* sbond = ssamp + TR;
     double* sxi = reinterpret_cast<double*>(sbond + TR);
     double* sxj = sxi + TR;
@@ -477,13 +479,16 @@ __global__ void __launch_bounds__(256) conn_terms_df_kernel(ModelDesc md, const 
     int* sj = si + TR;
     c128* lpn = reinterpret_cast<c128*>(((uintptr_t)(sj + TR) + 15) & ~(uintptr_t)15);
     const long long nconn = *nconn_ptr;
-    const long long c0 = (long long)blockIdx.x * TR;
-    if (c0 >= nconn) return;
-    const int rows = (int)((nconn - c0) < TR ? (nconn - c0) : TR);
     const int N = md.N;
+    // grid-stride over tiles of TR rows (the grid may be smaller than the list)
+    for (long long c0 = (long long)blockIdx.x * TR; c0 < nconn; c0 += (long long)gridDim.x * TR) {
+    df2* A = A0;
+    df2* B = B0;
+    const int rows = (int)((nconn - c0) < TR ? (nconn - c0) : TR);
     for (int r = threadIdx.x; r < TR; r += blockDim.x) {
         if (r < rows) {
-            const int s = csamp[c0 + r], b = cbond[c0 + r];
+            const long long c = cidx ? cidx[c0 + r] : c0 + r;
+            const int s = csamp[c], b = cbond[c];
             const int i = h.bond_ij[2 * b], j = h.bond_ij[2 * b + 1];
             ssamp[r] = s;
             sbond[r] = b;
@@ -566,7 +571,218 @@ __global__ void __launch_bounds__(256) conn_terms_df_kernel(ModelDesc md, const 
         double sn, cs;
         sincos(d.im, &sn, &cs);
         const double f = 2.0 * h.c * h.bond_J[sbond[r]] * (double)h.sign_rule;
-        terms[c0 + r] = mk<double>(f * m * cs, f * m * sn);
+        terms[cidx ? cidx[c0 + r] : c0 + r] = mk<double>(f * m * cs, f * m * sn);
+    }
+    __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ FP32 difference propagation
+// Local energies of FFNNs in the split precisions. Rather than pushing every connected
+// configuration x' through the network, the kernel propagates its differences to the parent
+// sample x: the first layer changes by dz = -2 x_i W[:, i] - 2 x_j W[:, j] (the bias cancels),
+// every hidden layer by
+//   dh = lncosh(z + dz) - lncosh(z) = log1p(w),
+//   w  = cosh(z + dz) / cosh(z) - 1 = 2 sinh(dz/2) (sinh(dz/2) + cosh(dz/2) tanh z),
+// (from cosh(z + dz) = cosh z cosh dz + sinh z sinh dz), the next pre-activation by W dh, and
+// ln psi(x') - ln psi(x) = W_L dh. The FP32 roundings then act on the differences, not on
+// the activations and ln psi, which are larger. z and tanh z come from the parent's FP64
+// forward. Re log1p(w) = ln|cosh z' / cosh z| has no branch; the imaginary part has to follow
+// the ln cosh branch of the exact forward (s = sign Re z), which differs from log1p's
+// principal value by 2 pi k. With s' = s, |Im dz| < 1/2 and |Im log1p w| < 5/2, k = 0
+// (each ln cosh is s Im z plus an angle in [-pi/2, pi/2], so the exact difference is within
+// pi + 1/2 of 0); otherwise k is taken from FP32 values of both ln cosh. A connection goes to
+// a list for the double-float kernel when FP32 cannot follow the exact forward: Re z' within
+// rounding of 0 while |Im z'| > 1.5 (there ln cosh jumps by 2 pi i), |1 + w| < 1e-3 (ln of
+// a near-zero cosh), or arguments outside the ranges of the FP32 functions.
+constexpr int DP_WARPS = 8;
+
+// (z, tanh z) of every hidden unit of the parent samples, FP32 copies of the FP64 forward
+__global__ void dp_parent_kernel(ModelDesc md, const c128* __restrict__ Z, long long ns, float4* __restrict__ pz) {
+    for (int l = 0; l + 1 < md.L; ++l) {
+        const long long n = ns * md.widths[l + 1];
+        const c128* z = Z + md.zoff[l];
+        float4* p = pz + md.zoff[l];
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+             e += (long long)gridDim.x * blockDim.x) {
+            const c128 v = z[e];
+            const c128 t = ctanh(v);
+            p[e] = make_float4((float)v.re, (float)v.im, (float)t.re, (float)t.im);
+        }
+    }
+}
+
+__global__ void weights_f32_kernel(const c128* __restrict__ w, long long n, float2* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)w[i].re, (float)w[i].im);
+}
+
+// dh of one hidden unit; p = (Re z, Im z, Re tanh z, Im tanh z) of the parent. *bad: the
+// connection needs the exact kernel.
+__device__ __forceinline__ float2 dp_lncosh_diff(float2 dz, float4 p, bool* bad) {
+    const float zr = p.x + dz.x, zi = p.y + dz.y;  // z' = z + dz
+    if (!(fabsf(dz.x) < 40.f && fabsf(dz.y) < 1e4f && p.z * p.z + p.w * p.w < 1e8f) ||
+        (fabsf(zr) < 2e-4f + 1e-5f * (fabsf(p.x) + fabsf(dz.x)) && fabsf(zi) > 1.5f)) {
+        *bad = true;
+        return make_float2(0.f, 0.f);
+    }
+    float sb, cb;
+    sincosf(0.5f * dz.y, &sb, &cb);
+    const float sa = sinhf(0.5f * dz.x), ca = coshf(0.5f * dz.x);
+    const float shr = sa * cb, shi = ca * sb;  // sinh(dz/2)
+    const float chr = ca * cb, chi = sa * sb;  // cosh(dz/2)
+    const float qr = shr + (chr * p.z - chi * p.w), qi = shi + (chr * p.w + chi * p.z);
+    const float wr = 2.f * (shr * qr - shi * qi), wi = 2.f * (shr * qi + shi * qr);
+    const float ar = 1.f + wr;
+    const float mod2 = ar * ar + wi * wi;  // |1 + w|^2
+    if (!(mod2 > 1e-6f)) {
+        *bad = true;
+        return make_float2(0.f, 0.f);
+    }
+    const float re = mod2 > 0.25f ? 0.5f * log1pf(fmaf(wr, wr, fmaf(wi, wi, 2.f * wr))) : 0.5f * logf(mod2);
+    float im = atan2f(wi, ar);
+    if ((zr >= 0.f) != (p.x >= 0.f) || fabsf(dz.y) >= 0.5f || fabsf(im) >= 2.5f) {
+        const float i1 = clncosh(mk<float>(zr, zi)).im, i0 = clncosh(mk<float>(p.x, p.y)).im;
+        im = fmaf(rintf((i1 - i0 - im) * 0.159154943f), 6.28318531f, im);
+    }
+    return make_float2(re, im);
+}
+
+// B[r][c] = sum_k A[r][k] W[k][c] for the RPW rows of this warp; lanes own columns c and c + 32
+// of every 64-column pass. A in shared memory (broadcast reads), W^T [in][out] from L1/L2.
+template <int RPW>
+__device__ __forceinline__ void dp_matvec(const float2* __restrict__ A, float2* __restrict__ B, int ld,
+                                          const float2* __restrict__ W, int in, int out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = warp * RPW;
+    for (int cb = 0; cb < out; cb += 64) {
+        const int c0 = cb + lane, c1 = cb + 32 + lane;
+        const bool v0 = c0 < out, v1 = c1 < out;
+        float2 a0[RPW], a1[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) a0[q] = a1[q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int k = 0; k < in; ++k) {
+            const float2 w0 = v0 ? __ldg(&W[(long long)k * out + c0]) : make_float2(0.f, 0.f);
+            const float2 w1 = v1 ? __ldg(&W[(long long)k * out + c1]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const float2 a = A[(r0 + q) * ld + k];
+                a0[q].x = fmaf(a.x, w0.x, fmaf(-a.y, w0.y, a0[q].x));
+                a0[q].y = fmaf(a.x, w0.y, fmaf(a.y, w0.x, a0[q].y));
+                a1[q].x = fmaf(a.x, w1.x, fmaf(-a.y, w1.y, a1[q].x));
+                a1[q].y = fmaf(a.x, w1.y, fmaf(a.y, w1.x, a1[q].y));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            if (v0) B[(r0 + q) * ld + c0] = a0[q];
+            if (v1) B[(r0 + q) * ld + c1] = a1[q];
+        }
+    }
+}
+
+// One tile of DP_WARPS * RPW connections per CTA; two [TR][ld] FP32 complex buffers in shared
+// memory (ld = widest hidden layer). Connections it cannot follow go to fb_list.
+template <int RPW>
+__global__ void __launch_bounds__(256) conn_terms_dp_kernel(ModelDesc md, const float2* __restrict__ w32,
+                                                             const float4* __restrict__ pz,
+                                                             const int8_t* __restrict__ x, HamDesc h,
+                                                             const int32_t* __restrict__ cbond,
+                                                             const int32_t* __restrict__ csamp,
+                                                             const long long* __restrict__ nconn_ptr, int ld,
+                                                             c128* __restrict__ terms, long long* __restrict__ fb_list,
+                                                             unsigned long long* __restrict__ fb_count, int fb_all) {
+    constexpr int TR = DP_WARPS * RPW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* D = reinterpret_cast<float2*>(smem_raw);  // dz of the current layer, then dh in place
+    float2* E = D + (size_t)TR * ld;                   // dz of the next layer
+    __shared__ int ssamp[TR], sbond[TR], si[TR], sj[TR], sflag[TR];
+    __shared__ float sxi[TR], sxj[TR];
+    __shared__ float2 sd[TR];
+    const long long nconn = *nconn_ptr;
+    const long long c0 = (long long)blockIdx.x * TR;
+    if (c0 >= nconn) return;
+    const int rows = (int)((nconn - c0) < TR ? (nconn - c0) : TR);
+    const int N = md.N;
+    for (int r = threadIdx.x; r < TR; r += blockDim.x) {
+        int s = 0, b = 0, i = 0, j = 0;
+        float xi = 0.f, xj = 0.f;
+        if (r < rows) {  // rows past the end repeat sample 0 with zero spins and are not written
+            s = csamp[c0 + r];
+            b = cbond[c0 + r];
+            i = h.bond_ij[2 * b];
+            j = h.bond_ij[2 * b + 1];
+            xi = (float)x[(long long)s * N + i];
+            xj = (float)x[(long long)s * N + j];
+        }
+        ssamp[r] = s;
+        sbond[r] = b;
+        si[r] = i;
+        sj[r] = j;
+        sxi[r] = xi;
+        sxj[r] = xj;
+        sflag[r] = 0;
+    }
+    __syncthreads();
+    {  // first layer: dz = -2 x_i W[:, i] - 2 x_j W[:, j] (one rounding)
+        const int out0 = md.widths[1];
+        const float2* W0 = w32 + md.wtoff[0];  // [N][out0]
+        for (int idx = threadIdx.x; idx < TR * out0; idx += blockDim.x) {
+            const int r = idx / out0, u = idx - r * out0;
+            const float2 wi = W0[(long long)si[r] * out0 + u], wj = W0[(long long)sj[r] * out0 + u];
+            const float ai = -2.f * sxi[r], aj = -2.f * sxj[r];
+            D[r * ld + u] = make_float2(fmaf(ai, wi.x, aj * wj.x), fmaf(ai, wi.y, aj * wj.y));
+        }
+    }
+    __syncthreads();
+    for (int l = 0; l + 1 < md.L; ++l) {
+        const int out = md.widths[l + 1];
+        const float4* P = pz + md.zoff[l];
+        for (int idx = threadIdx.x; idx < TR * out; idx += blockDim.x) {
+            const int r = idx / out, u = idx - r * out;
+            bool bad = false;
+            const float2 dh = dp_lncosh_diff(D[r * ld + u], P[(long long)ssamp[r] * out + u], &bad);
+            if (bad) sflag[r] = 1;
+            D[r * ld + u] = dh;
+        }
+        __syncthreads();
+        const int nout = md.widths[l + 2];
+        const float2* Wn = w32 + md.wtoff[l + 1];  // [out][nout]
+        if (l + 2 == md.L) {  // output layer (one unit): a dot product per row
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int q = 0; q < RPW; ++q) {
+                const int r = warp * RPW + q;
+                float re = 0.f, im = 0.f;
+                for (int k = lane; k < out; k += 32) {
+                    const float2 a = D[r * ld + k], w = __ldg(&Wn[k]);
+                    re = fmaf(a.x, w.x, fmaf(-a.y, w.y, re));
+                    im = fmaf(a.x, w.y, fmaf(a.y, w.x, im));
+                }
+                re = warp_sum(re);
+                im = warp_sum(im);
+                if (lane == 0) sd[r] = make_float2(re, im);
+            }
+        } else {
+            dp_matvec<RPW>(D, E, ld, Wn, out, nout);
+            float2* t = D;
+            D = E;
+            E = t;
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const long long c = c0 + r;
+        const float2 d = sd[r];  // ln psi(x') - ln psi(x)
+        if (fb_all || sflag[r] || !(fabsf(d.x) < 80.f) || !(fabsf(d.y) < 1e6f)) {
+            fb_list[atomicAdd(fb_count, 1ull)] = c;
+        } else {
+            const double m = exp((double)d.x);
+            double sn, cs;
+            sincos((double)d.y, &sn, &cs);
+            const double f = 2.0 * h.c * h.bond_J[sbond[r]] * (double)h.sign_rule;
+            terms[c] = mk<double>(f * m * cs, f * m * sn);
+        }
     }
 }
 
@@ -676,7 +892,8 @@ cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, co
         count_launch();
         conn_terms_df_kernel<<<(unsigned)grid, 256, smem, st>>>(md, (const c128*)thR, (const c128*)wtR,
                                                                  (const float4*)wdf, (const c128*)Z, logpsi, x, h,
-                                                                 conn_bond, conn_sample, nconn_ptr, TR, terms);
+                                                                 conn_bond, conn_sample, nconn_ptr, nullptr, TR,
+                                                                 terms);
         return cudaGetLastError();
     }
     return prec == NQS_FP64
@@ -684,6 +901,72 @@ cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, co
                                       terms, st)
                : conn_terms_t<float>(md, thR, wtR, Z, logpsi, x, h, conn_bond, conn_sample, nconn_ptr, max_conn,
                                      terms, st);
+}
+
+bool dp_applicable(const ModelDesc& md) {
+    if (md.kind != NQS_FFNN || md.L < 2 || md.widths[md.L] != 1) return false;
+    return dp_width(md) <= 512;
+}
+int dp_width(const ModelDesc& md) {
+    int w = 0;
+    for (int l = 1; l < md.L; ++l) w = md.widths[l] > w ? md.widths[l] : w;
+    return w;
+}
+
+cudaError_t launch_conn_terms_dp(const ModelDesc& md, const void* thR, const void* wtR, const void* wdf,
+                                 const void* Z, const c128* logpsi, const int8_t* x, long long ns, const HamDesc& h,
+                                 const int32_t* conn_bond, const int32_t* conn_sample, const long long* nconn_ptr,
+                                 long long max_conn, c128* terms, const DpBufs& b, cudaStream_t st) {
+    if (max_conn <= 0) return cudaSuccess;
+    const long long we = model_wt_elems(md);
+    count_launch();
+    weights_f32_kernel<<<(unsigned)((we + 255) / 256 < 1024 ? (we + 255) / 256 : 1024), 256, 0, st>>>(
+        (const c128*)wtR, we, b.w32);
+    count_launch();
+    dp_parent_kernel<<<1024, 256, 0, st>>>(md, (const c128*)Z, ns, b.pz);
+    cudaError_t e = cudaMemsetAsync(b.fb_count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    // rows per warp: two [TR][ld] FP32 complex buffers within 96 KB (two CTAs per SM)
+    const int ld = dp_width(md);
+    const int rpw = ld <= 96 ? 8 : (ld <= 192 ? 4 : (ld <= 384 ? 2 : 1));
+    const int TR = DP_WARPS * rpw;
+    const size_t smem = 2ull * TR * ld * sizeof(float2);
+    const long long grid = (max_conn + TR - 1) / TR;
+    const int fb_all = dp_fallback_all() ? 1 : 0;
+    count_launch();
+#define NQS_DP_LAUNCH(R)                                                                                     \
+    do {                                                                                                     \
+        e = cudaFuncSetAttribute(conn_terms_dp_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                 (int)smem);                                                                 \
+        if (e != cudaSuccess) return e;                                                                      \
+        conn_terms_dp_kernel<R><<<(unsigned)grid, 256, smem, st>>>(md, b.w32, b.pz, x, h, conn_bond,         \
+                                                                   conn_sample, nconn_ptr, ld, terms,       \
+                                                                   b.fb_list, b.fb_count, fb_all);          \
+    } while (0)
+    if (rpw == 8) NQS_DP_LAUNCH(8);
+    else if (rpw == 4) NQS_DP_LAUNCH(4);
+    else if (rpw == 2) NQS_DP_LAUNCH(2);
+    else NQS_DP_LAUNCH(1);
+#undef NQS_DP_LAUNCH
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the listed connections in double-float (every CTA past the list's end returns at once)
+    e = launch_split_weights(md, wtR, const_cast<void*>(wdf), st);
+    if (e != cudaSuccess) return e;
+    long long tr = 180000LL / (2LL * md.maxw * (long long)sizeof(c128));
+    tr = tr > 32 ? 32 : tr;
+    tr = (tr / 4) * 4;
+    const int TRf = tr < 4 ? 4 : (int)tr;
+    const size_t smf = 2ull * TRf * md.maxw * sizeof(c128) + (size_t)TRf * (4 * sizeof(int) + 2 * sizeof(double)) +
+                       16 + (size_t)TRf * sizeof(c128);
+    e = cudaFuncSetAttribute(conn_terms_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    const long long tiles = (max_conn + TRf - 1) / TRf;
+    conn_terms_df_kernel<<<(unsigned)(tiles < 1024 ? tiles : 1024), 256, smf, st>>>(
+        md, (const c128*)thR, (const c128*)wtR, (const float4*)wdf, (const c128*)Z, logpsi, x, h, conn_bond,
+        conn_sample, reinterpret_cast<const long long*>(b.fb_count), b.fb_list, TRf, terms);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_eloc_reduce(const int8_t* x, long long ns, const HamDesc& h, const long long* off,

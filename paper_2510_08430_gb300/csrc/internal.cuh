@@ -63,6 +63,21 @@ cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, co
                               const void* Z, const c128* logpsi, const int8_t* x, const HamDesc& h,
                               const int32_t* conn_bond, const int32_t* conn_sample,
                               const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st);
+// FP32 difference propagation of the connected forwards (FFNN, split precisions), with the
+// connections it cannot follow recomputed in double-float
+struct DpBufs {
+    float2* w32;                    // FP32 copy of the transposed weights [model_wt_elems]
+    float4* pz;                     // (z, tanh z) of the parents' hidden units [model_z_elems]
+    long long* fb_list;             // connections for the double-float kernel [max_conn]
+    unsigned long long* fb_count;   // their number
+};
+bool dp_fallback_all();                   // test hook: every connection to the double-float kernel
+int dp_width(const ModelDesc& md);        // widest hidden layer
+bool dp_applicable(const ModelDesc& md);  // FFNN, >= 2 weight layers, one output, hidden width <= 512
+cudaError_t launch_conn_terms_dp(const ModelDesc& md, const void* thR, const void* wtR, const void* wdf,
+                                 const void* Z, const c128* logpsi, const int8_t* x, long long ns, const HamDesc& h,
+                                 const int32_t* conn_bond, const int32_t* conn_sample, const long long* nconn_ptr,
+                                 long long max_conn, c128* terms, const DpBufs& b, cudaStream_t st);
 cudaError_t launch_eloc_reduce(const int8_t* x, long long ns, const HamDesc& h,
                                const long long* off, const c128* terms, c128* eloc,
                                DevStatus* status, cudaStream_t st);

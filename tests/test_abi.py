@@ -99,6 +99,7 @@ def test_newer_entry_points_validate_on_the_host(lib):
     # test hook: negative limits are rejected, zeros restore the defaults
     assert lib.nqs_set_limits(-1, 0) == -1 and lib.nqs_set_limits(0, -5) == -1
     assert lib.nqs_set_limits(0, 0) == 0
+    assert lib.nqs_set_eloc_fallback_all(1) == 0 and lib.nqs_set_eloc_fallback_all(0) == 0
     # shard sums and VJP: leading dimension below n_s
     assert lib.nqs_shard_sums(fake, 10, 64, 10, 0, fake, fake, fake, None) == -1
     assert lib.nqs_vjp(fake, 10, 64, 10, 0, fake, fake, None) == -1
