@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--param-space", action="store_true",
                     help="solve every block in parameter space (profiling of reduced-N_s cases with the "
                          "full-size kernels)")
+    ap.add_argument("--eloc", default="diff32", choices=["diff32", "fp64"],
+                    help="local energies: FP32 difference propagation (NQS_ELOC_DIFF32; its dtheta is checked "
+                         "against the FP64 oracle in the same run) or the FP64-class arithmetic")
     ap.add_argument("--sharded", action="store_true",
                     help="split ONE instance over the ranks by samples (three exchanges over NCCL; strong scaling)")
     return ap.parse_args()
@@ -61,7 +64,11 @@ SOLVER_DESC = {"fp64": "FP64 Householder eigensolver",
                         "||S_b||_F; FP32 Householder + refinement, then FP64 eigensolver, as fallbacks)"}
 
 
-def workload_desc(w, solver="mixed") -> dict:
+ELOC_DESC = {"diff32": "FP32 difference propagation of the connected forwards (exact fallback list)",
+             "fp64": "FP64 connected forwards (double-float hidden layers)"}
+
+
+def workload_desc(w, solver="mixed", eloc="fp64") -> dict:
     import numpy as np
     return {
         "workload": f"{w.name}: widths {[int(v) for v in w.model.widths]}, {int(w.bond_ij.shape[0])} bonds, "
@@ -72,6 +79,7 @@ def workload_desc(w, solver="mixed") -> dict:
         "n_p": int(w.model.n_params),
         "blocks": [int(v) for v in np.diff(w.block_off)],
         "precision": w.precision,
+        "local_energy": ELOC_DESC[eloc],
         "diag_shift": w.diag_shift,
         "cutoff": w.cutoff,
         "l2": "flushed between timed steps (256 MB write); each step also streams > 2 GB",
@@ -359,7 +367,7 @@ def run_reference(args, rank: int, world: int) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_desc(w, "mixed"),
+        "config": workload_desc(w, "mixed", args.eloc),
         "reference_impl": "FP64 NumPy oracle (same workload and metric; FP64 Jacobian, E_loc, Gram and LAPACK eigh)",
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": info["cores"], "threads": info["threads"],
                          "kind": "oracle", "sample": info["sample"], "stage_seconds": info["stage_seconds"]},
@@ -398,7 +406,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         gram_tuning = {"group": rec[key]["group"], "candidates_ms": rec[key]["ms"],
                        "what": "edge G of the square groups of 128x128 tiles the persistent Gram takes in turn"}
     step = nq.SRStep(model, w.n_samples, ham, w.block_off, w.precision, w.diag_shift, w.cutoff, solver=args.solver,
-                     param_space=args.param_space)
+                     param_space=args.param_space, eloc_diff32=args.eloc == "diff32")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -507,7 +515,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
-        "config": dict(workload_desc(w, args.solver), parallelism=("replicas" if world > 1 else "single")),
+        "config": dict(workload_desc(w, args.solver, args.eloc), parallelism=("replicas" if world > 1 else "single")),
         "stage_ms": st_mean,
         "gram_tuning": gram_tuning,
         "dtheta_within_tol": acc["within"],
@@ -594,7 +602,8 @@ def run_sharded(args, rank: int, world: int, local_rank: int) -> None:
     idx = np.array_split(np.arange(w.n_samples), world)[rank]
     theta = torch.as_tensor(w.theta, device="cuda")
     x = torch.as_tensor(w.configs[idx], device="cuda")
-    be = sharded.LibraryShardBackend(model, ham, w.block_off, w.precision, args.solver)
+    be = sharded.LibraryShardBackend(model, ham, w.block_off, w.precision, args.solver,
+                                     eloc_diff32=args.eloc == "diff32")
     comm = sharded.TorchComm() if world > 1 else _LocalComm()
 
     def step():
@@ -631,7 +640,7 @@ def run_sharded(args, rank: int, world: int, local_rank: int) -> None:
         "metric": METRIC, "value": args.steps / t_max, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": dtype_of(w.precision), "data": "synthetic",
-        "config": dict(workload_desc(w, args.solver), parallelism=f"samples sharded over {world} ranks",
+        "config": dict(workload_desc(w, args.solver, args.eloc), parallelism=f"samples sharded over {world} ranks",
                        exchanges="all-reduce of shard sums (n_p + 1 complex); reduce of S_b, F_b to block owners; "
                                  "all-gather of owners' dtheta"),
         "dtheta_within_tol": acc["within"], "accuracy": acc, "clocks": clk, "gpu_launches": int(launches),

@@ -79,20 +79,28 @@ extern "C" {
  *                   fifteen products (every term above 2^-32 of the group scale) per group,
  *                   groups summed in double-float. Better than FP32 rounding of the data
  *                   even on heavy-tailed Jacobian rows.
- * Local energies in the split modes: RBMs and one-layer networks as in NQS_FP64; FFNNs by
- * FP32 difference propagation: for every connected configuration x' the changes of the
- * pre-activations dz and of the hidden units dh = lncosh(z + dz) - lncosh(z) =
- * log1p(2 sinh(dz/2) (sinh(dz/2) + cosh(dz/2) tanh z)) relative to the parent sample x
- * (z and tanh z from its FP64 forward) are carried through the layers in FP32, following
- * the ln cosh branch of the exact forward, so that ln psi(x') - ln psi(x) carries FP32
- * rounding of the differences only (about 1e-7 relative on E_loc); the rare connections
- * whose branch or range FP32 cannot decide are recomputed in the NQS_FP64 arithmetic.
- * The sr_step flag NQS_ELOC_FP64 selects the NQS_FP64 local energies instead.
- * The per-block shifted eigen-decomposition and solve is selected separately (solver
- * argument, below). */
+ * Local energies in the split modes are those of NQS_FP64 unless the flag NQS_ELOC_DIFF32
+ * (below) is given. The per-block shifted eigen-decomposition and solve is selected
+ * separately (solver argument, below). */
 typedef enum {
     NQS_FP64 = 0, NQS_FP32 = 1, NQS_SPLIT_BF16 = 2, NQS_SPLIT_BF16X3 = 3, NQS_SPLIT_BF16_EXACT = 4
 } nqs_precision;
+
+/* NQS_ELOC_DIFF32 (flag of sr_step, sr_step_batched and nqs_local_energy_ex; any precision
+ * but NQS_FP32): FFNN local energies by FP32 difference propagation. For every connected
+ * configuration x' the changes of the pre-activations dz and of the hidden units
+ * dh = lncosh(z + dz) - lncosh(z) = log1p(2 sinh(dz/2) (sinh(dz/2) + cosh(dz/2) tanh z))
+ * relative to the parent sample x (z and tanh z from its FP64 forward) are carried through
+ * the layers in FP32, following the ln cosh branch of the exact forward, so that
+ * ln psi(x') - ln psi(x) carries FP32 rounding of the differences only; the rare connections
+ * whose branch or range FP32 cannot decide are recomputed in the NQS_FP64 arithmetic. The
+ * per-sample error is about 1e-8 of |E_loc| (heavy-tailed, up to ~1e-6). Its effect on
+ * dtheta scales with that error over the spread of E_loc across the samples: small when the
+ * local energies fluctuate by more than ~1e-3 of their size (the J1-J2 lattices with shallow
+ * FFNNs: rms error / spread below 5e-7), too large for states whose E_loc is nearly constant
+ * (deep random networks: 1e-4 and more), which need the default arithmetic. RBMs and
+ * one-layer networks always take the NQS_FP64 arithmetic. */
+#define NQS_ELOC_DIFF32 8
 
 enum { NQS_RBM = 0, NQS_FFNN = 1 };
 
@@ -179,12 +187,16 @@ NQS_API int nqs_vjp(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_
 /* nqs_local_energy -- E_loc(x_s) (Eq. 1) for the Hamiltonian h:
  *   E_loc(x) = c sum_b J_b [ x_i x_j + [x_i != x_j] 2 sign_rule psi(x^{ij})/psi(x) ],
  * x^{ij} = x with spins i and j flipped; connected configurations are visited in
- * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32; FP64 for NQS_FP64, with
- * the FFNN hidden layers of the connected forwards in double-float (about 2^-46 relative);
- * the split precisions as described under nqs_precision (FFNN: FP32 difference propagation). */
+ * bond order. eloc_out: c128 [n_s]. Arithmetic in FP32 for NQS_FP32; otherwise FP64, with
+ * the FFNN hidden layers of the connected forwards in double-float (about 2^-46 relative).
+ * nqs_local_energy_ex takes flags: 0 or NQS_ELOC_DIFF32 (not with NQS_FP32); other bits are
+ * NQS_ERR_INVALID_ARG. Same workspace size. */
 NQS_API int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
                      const nqs_hamiltonian* h, int32_t precision, void* eloc_out,
                      nqs_workspace* ws, void* stream);
+NQS_API int nqs_local_energy_ex(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
+                        const nqs_hamiltonian* h, int32_t precision, int32_t flags, void* eloc_out,
+                        nqs_workspace* ws, void* stream);
 
 /* nqs_connections -- the integer work of E_loc: for every sample, the bonds with
  * x_i != x_j in bond order. conn_count: int32 [n_s]; conn_offset: int64 [n_s+1]
@@ -338,8 +350,8 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
  *   evals_out / n_kept_out as in qgt_block_solve (may be NULL).
  *   flags: NQS_SYNC makes the call synchronise and return device status.
  *          NQS_PARAM_SPACE solves every block in parameter space (see below).
- *          NQS_ELOC_FP64 computes the local energies of the split precisions in the
- *          FP64-class arithmetic of NQS_FP64 instead of FP32 difference propagation.
+ *          NQS_ELOC_DIFF32 computes FFNN local energies by FP32 difference propagation
+ *          (see above).
  *          NQS_GRAPH makes the call capturable into a CUDA graph (stream capture):
  *          nothing synchronises with the host. The mixed solver's certificate is then
  *          checked on the device; when it fails the step's dtheta is not the definition's
@@ -350,7 +362,6 @@ NQS_API int qgt_block_solve(void* S_packed, const int64_t* block_off, int32_t n_
 #define NQS_SYNC 1
 #define NQS_GRAPH 2
 #define NQS_PARAM_SPACE 4
-#define NQS_ELOC_FP64 8
 /* Blocks wider than the sample count. With the mixed solver, diag_shift > 0, precision
  * NQS_FP64 or NQS_SPLIT_BF16_EXACT and no NQS_PARAM_SPACE flag, a block with n_b > n_s is
  * solved in sample space (push-through identity):
@@ -438,7 +449,7 @@ NQS_API int qgt_inverse_diagnostics(const void* S_a, const int64_t* block_off_a,
 NQS_API int nqs_set_limits(int32_t max_sweeps, int64_t wait_ns);
 
 /* nqs_set_eloc_fallback_all -- test hook (process-wide): on != 0 sends every connection of
- * the FP32 difference-propagation local energies (split precisions, FFNN) to the FP64-class
+ * the FP32 difference-propagation local energies (NQS_ELOC_DIFF32) to the FP64-class
  * kernel that otherwise recomputes only the connections FP32 cannot follow, so that this
  * path can be checked on its own; the results are then those of NQS_FP64. 0 restores. */
 NQS_API int nqs_set_eloc_fallback_all(int32_t on);

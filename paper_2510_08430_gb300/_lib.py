@@ -25,7 +25,7 @@ NQS_RBM, NQS_FFNN = 0, 1
 NQS_SYNC = 1
 NQS_GRAPH = 2
 NQS_PARAM_SPACE = 4
-NQS_ELOC_FP64 = 8
+NQS_ELOC_DIFF32 = 8
 NQS_SOLVE_FP64, NQS_SOLVE_MIXED, NQS_SOLVE_MIXED_PSD = 0, 1, 2
 NQS_STATIC_MAX_SAMPLES = 65536
 
@@ -64,6 +64,7 @@ SIGNATURES = {
     "qgt_packed_size": (C.c_int64, [OFF, I32]),
     "nqs_jacobian": (C.c_int, [MP, P, P, I64, I32, P, P, I64, P, P]),
     "nqs_local_energy": (C.c_int, [MP, P, P, I64, HP, I32, P, P, P]),
+    "nqs_local_energy_ex": (C.c_int, [MP, P, P, I64, HP, I32, I32, P, P, P]),
     "nqs_connections": (C.c_int, [P, I64, HP, P, P, P, I64, C.POINTER(C.c_int64), P, P]),
     "nqs_vjp": (C.c_int, [P, I64, I64, I64, I32, P, P, P]),
     "ntk_solve_workspace_size": (C.c_int, [I64, I64, I32, SZ]),

@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16_EXACT, NQS_SPLIT_BF16X3,
-                   NQS_ELOC_FP64, NQS_GRAPH, NQS_PARAM_SPACE, NQS_SYNC, check, nqs_hamiltonian, nqs_model)
+                   NQS_ELOC_DIFF32, NQS_GRAPH, NQS_PARAM_SPACE, NQS_SYNC, check, nqs_hamiltonian, nqs_model)
 
 PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3,
               "split_bf16_exact": NQS_SPLIT_BF16_EXACT}
@@ -185,7 +185,9 @@ def log_psi(model: "Model", theta: torch.Tensor, configs: torch.Tensor, precisio
 
 
 def nqs_local_energy(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian,
-                     precision="fp64", ws: Optional[Workspace] = None, sync: bool = True) -> torch.Tensor:
+                     precision="fp64", ws: Optional[Workspace] = None, sync: bool = True,
+                     diff32: bool = False) -> torch.Tensor:
+    """E_loc c128 [n_s]; diff32: FP32 difference propagation (nqs_local_energy_ex, NQS_ELOC_DIFF32)."""
     lib = _lib.load()
     p = _prec(precision)
     ns = int(configs.shape[0])
@@ -193,8 +195,8 @@ def nqs_local_energy(model: Model, theta: torch.Tensor, configs: torch.Tensor, h
     ws.ensure(_size(lib.nqs_local_energy_workspace_size, C.byref(model.c), ns, C.byref(ham.c), p))
     eloc = torch.empty(ns, dtype=torch.complex128, device=configs.device)
     with _on(theta, configs, ham.bond_ij):
-        check(lib.nqs_local_energy(C.byref(model.c), _ptr(theta), _ptr(configs), ns, C.byref(ham.c), p, _ptr(eloc),
-                                   ws.h, _stream()))
+        check(lib.nqs_local_energy_ex(C.byref(model.c), _ptr(theta), _ptr(configs), ns, C.byref(ham.c), p,
+                                      NQS_ELOC_DIFF32 if diff32 else 0, _ptr(eloc), ws.h, _stream()))
     if sync:
         ws.sync_status()
     return eloc
@@ -292,7 +294,7 @@ class SRStep:
     def __init__(self, model: Model, n_s: int, ham: Hamiltonian, block_off, precision="split_bf16x3",
                  diag_shift: float = 1e-3, cutoff: float = 1e-10, cutoff_mode: int = 0, eta: float = 1.0,
                  want_evals: bool = False, solver="fp64", device="cuda", param_space: bool = False,
-                 eloc_fp64: bool = False):
+                 eloc_diff32: bool = False):
         lib = _lib.load()
         self.model, self.ham = model, ham
         self.n_s = int(n_s)
@@ -303,7 +305,7 @@ class SRStep:
         self.n_p = int(block_off[-1])
         self.shift, self.cutoff, self.mode, self.eta = float(diag_shift), float(cutoff), int(cutoff_mode), float(eta)
         # blocks wider than n_s are solved in sample space unless param_space is set
-        self.flags = (NQS_PARAM_SPACE if param_space else 0) | (NQS_ELOC_FP64 if eloc_fp64 else 0)
+        self.flags = (NQS_PARAM_SPACE if param_space else 0) | (NQS_ELOC_DIFF32 if eloc_diff32 else 0)
         self.ws = Workspace(_size(lib.sr_step_workspace_size2, C.byref(model.c), self.n_s, C.byref(ham.c), self.off,
                                   self.nb, self.shift, self.p, self.solver, self.flags), device=device)
         self.dtheta = torch.empty(self.n_p, dtype=torch.complex128, device=device)
@@ -361,18 +363,18 @@ class SRStep:
 
 def sr_step(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian, block_off,
             diag_shift: float, cutoff: float, eta: float = 1.0, precision="fp64", cutoff_mode: int = 0,
-            want_evals: bool = True, solver="fp64", param_space: bool = False, eloc_fp64: bool = False):
-    """One whole block-layer SR step: (dtheta, Emean, evals, n_kept). eloc_fp64: FP64-class
-    local energies in the split precisions (default: FP32 difference propagation)."""
+            want_evals: bool = True, solver="fp64", param_space: bool = False, eloc_diff32: bool = False):
+    """One whole block-layer SR step: (dtheta, Emean, evals, n_kept). eloc_diff32: FFNN local
+    energies by FP32 difference propagation (NQS_ELOC_DIFF32) instead of FP64-class arithmetic."""
     st = SRStep(model, int(configs.shape[0]), ham, block_off, precision, diag_shift, cutoff, cutoff_mode, eta,
-                want_evals, solver, device=configs.device, param_space=param_space, eloc_fp64=eloc_fp64)
+                want_evals, solver, device=configs.device, param_space=param_space, eloc_diff32=eloc_diff32)
     st(theta, configs, sync=True)
     return st.dtheta, st.emean, st.evals, st.n_kept
 
 
 def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float, cutoff: float, eta: float = 1.0,
                     precision="split_bf16", cutoff_mode: int = 0, solver="mixed", want_evals: bool = False,
-                    eloc_fp64: bool = False):
+                    eloc_diff32: bool = False):
     """Several independent SR steps in one call (one grouped Gram and one eigensolver launch).
     Lists of per-instance Model, theta (c128 device), configs (int8 device), Hamiltonian and block
     offsets. Returns (list of dtheta, Emean c128 [n_inst], evals or None, n_kept int32 [sum blocks])."""
@@ -399,7 +401,7 @@ def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float
     with _on(th, xc):
         check(lib.sr_step_batched(n, mods, _ptr(th), _ptr(xc), ns, hs, off_c, nbs, float(diag_shift), float(cutoff),
                                   int(cutoff_mode), float(eta), p, _solver(solver), _ptr(dth), _ptr(em), _ptr(ev),
-                                  _ptr(nk), NQS_SYNC | (NQS_ELOC_FP64 if eloc_fp64 else 0), ws.h, _stream()))
+                                  _ptr(nk), NQS_SYNC | (NQS_ELOC_DIFF32 if eloc_diff32 else 0), ws.h, _stream()))
     sizes = [int(o[-1]) for o in block_offs]
     return list(torch.split(dth, sizes)), em, ev, nk
 

@@ -118,12 +118,10 @@ inline int jac_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
 // local energies: FP32 arithmetic only in NQS_FP32 mode (in the split modes an FP32
 // E_loc alone moves dtheta by ~1e-5 relative on the 10x10 workload)
 inline int eloc_prec(int prec) { return prec == NQS_FP32 ? NQS_FP32 : NQS_FP64; }
-// split precisions: FFNN local energies by FP32 difference propagation (the FP64-class
-// double-float kernel for the connections it cannot follow) unless NQS_ELOC_FP64 is set
-inline bool eloc_dp(int prec, int flags) {
-    return (prec == NQS_SPLIT_BF16 || prec == NQS_SPLIT_BF16X3 || prec == NQS_SPLIT_BF16_EXACT) &&
-           !(flags & NQS_ELOC_FP64);
-}
+// NQS_ELOC_DIFF32: FFNN local energies by FP32 difference propagation (the FP64-class
+// double-float kernel for the connections it cannot follow); needs the FP64 forward of the
+// parents, i.e. any precision but NQS_FP32
+inline bool eloc_dp(int prec, int flags) { return (flags & NQS_ELOC_DIFF32) && prec != NQS_FP32; }
 inline int nsplit_of(int prec) {
     return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : (prec == NQS_SPLIT_BF16_EXACT ? 5 : 0));
 }
@@ -817,9 +815,17 @@ int nqs_vjp(const void* O, int64_t ldo, int64_t n_s, int64_t n_p, int32_t precis
 
 int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
                      const nqs_hamiltonian* h, int32_t precision, void* eloc_out, nqs_workspace* ws, void* stream) {
+    return nqs_local_energy_ex(m, theta, configs, n_s, h, precision, 0, eloc_out, ws, stream);
+}
+
+int nqs_local_energy_ex(const nqs_model* m, const void* theta, const int8_t* configs, int64_t n_s,
+                        const nqs_hamiltonian* h, int32_t precision, int32_t flags, void* eloc_out,
+                        nqs_workspace* ws, void* stream) {
     ModelDesc md;
     HamDesc hd;
     if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
+    if ((flags & ~NQS_ELOC_DIFF32) || ((flags & NQS_ELOC_DIFF32) && precision == NQS_FP32))
+        return fail(NQS_ERR_INVALID_ARG, "nqs_local_energy_ex: bad flags (NQS_ELOC_DIFF32 needs an FP64 forward)");
     if (n_s < 1 || !theta || !configs || !eloc_out) return fail(NQS_ERR_INVALID_ARG, "nqs_local_energy: bad arguments");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
     int rc = ham_desc(h, md.N, &hd);
@@ -836,7 +842,7 @@ int nqs_local_energy(const nqs_model* m, const void* theta, const int8_t* config
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
     return run_eloc(md, rp, hd, configs, n_s, jb, eb, static_cast<c128*>(eloc_out), status_of(ws), st,
-                    eloc_dp(precision, 0));
+                    eloc_dp(precision, flags));
 }
 
 int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h, int32_t* conn_count,
@@ -1032,6 +1038,8 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     if (check_prec(precision)) return NQS_ERR_INVALID_ARG;
     if (n_s < 1 || !theta || !configs || !dtheta_out || !Emean_out)
         return fail(NQS_ERR_INVALID_ARG, "sr_step: bad arguments");
+    if ((flags & NQS_ELOC_DIFF32) && precision == NQS_FP32)
+        return fail(NQS_ERR_INVALID_ARG, "sr_step: NQS_ELOC_DIFF32 needs an FP64 forward (not NQS_FP32)");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
     int rc = ham_desc(h, md.N, &hd);
     if (rc) return rc;

@@ -75,17 +75,19 @@ def owned_unpack(buf: torch.Tensor, block_off, owned: Sequence[int]):
 class LibraryShardBackend:
     """One shard's compute through the C ABI (device tensors)."""
 
-    def __init__(self, model: Model, ham: Hamiltonian, block_off, precision="fp64", solver="fp64"):
+    def __init__(self, model: Model, ham: Hamiltonian, block_off, precision="fp64", solver="fp64",
+                 eloc_diff32: bool = False):
         self.model, self.ham = model, ham
         self.block_off = np.asarray(block_off, dtype=np.int64)
         self.precision, self.solver = precision, solver
+        self.eloc_diff32 = eloc_diff32
         self.n_p = int(self.block_off[-1])
 
     def local(self, theta: torch.Tensor, configs: torch.Tensor):
         """Jacobian, local energies and the shard sums: (state, osum [n_p], esum [1])."""
         lib = _lib.load()
         _, O = nqs_jacobian(self.model, theta, configs, self.precision)
-        eloc = nqs_local_energy(self.model, theta, configs, self.ham, self.precision)
+        eloc = nqs_local_energy(self.model, theta, configs, self.ham, self.precision, diff32=self.eloc_diff32)
         osum = torch.empty(self.n_p, dtype=torch.complex128, device=O.device)
         esum = torch.empty(1, dtype=torch.complex128, device=O.device)
         ns = int(configs.shape[0])

@@ -29,3 +29,15 @@ def unpack_lower(S_packed: np.ndarray, block_off):
         out.append(np.tril(m))
         p += n * n
     return out
+
+
+# Per-sample local-energy bar of the FP32 difference propagation (NQS_ELOC_DIFF32), relative
+# to max(|E_loc|, 1); FP64-class local energies are held to 1e-12.
+ELOC_SPLIT_BAR = 2e-6
+
+
+def emean_bar(n_s: int, diff32: bool) -> float:
+    """Relative bar on <E>: 1e-12 with FP64-class local energies; with the FP32 difference
+    propagation the per-sample rounding errors (round to nearest, independent between
+    samples) average down, so the mean is held to ELOC_SPLIT_BAR / sqrt(n_s)."""
+    return max(ELOC_SPLIT_BAR / np.sqrt(n_s), 1e-12) if diff32 else 1e-12

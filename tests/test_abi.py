@@ -100,6 +100,14 @@ def test_newer_entry_points_validate_on_the_host(lib):
     assert lib.nqs_set_limits(-1, 0) == -1 and lib.nqs_set_limits(0, -5) == -1
     assert lib.nqs_set_limits(0, 0) == 0
     assert lib.nqs_set_eloc_fallback_all(1) == 0 and lib.nqs_set_eloc_fallback_all(0) == 0
+    # local energies: unknown flag bits, and the difference propagation without an FP64 forward
+    from paper_2510_08430_gb300 import _lib
+    m = _model(1, [36, 64, 64, 1])
+    h = _lib.nqs_hamiltonian(36, 144, None, None, 1.0, 1)
+    assert lib.nqs_local_energy_ex(C.byref(m.c), fake, fake, 8, C.byref(h), 4, 16, fake, None, None) == -1
+    assert lib.nqs_local_energy_ex(C.byref(m.c), fake, fake, 8, C.byref(h), 1, _lib.NQS_ELOC_DIFF32, fake, None,
+                                   None) == -1
+    assert b"NQS_ELOC_DIFF32" in lib.nqs_last_error()
     # shard sums and VJP: leading dimension below n_s
     assert lib.nqs_shard_sums(fake, 10, 64, 10, 0, fake, fake, fake, None) == -1
     assert lib.nqs_vjp(fake, 10, 64, 10, 0, fake, fake, None) == -1

@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import workloads as W
-from gpu_util import dev_inputs, rel, unpack_lower
+from gpu_util import ELOC_SPLIT_BAR, dev_inputs, emean_bar, rel, unpack_lower
 
 pytestmark = pytest.mark.gpu
 
@@ -68,23 +68,26 @@ def test_connections_bit_exact(name, ns):
     ("j1j2_6x6_ffnn", 40, "fp64", 1e-12),
     ("j1j2_6x6_ffnn", 40, "fp32", 1e-5),
     ("j1j2_10x10_ffnn5", 12, "fp32", 1e-5),
+    ("j1j2_6x6_ffnn", 40, "split_bf16_exact", 1e-12),
     # FP32 difference propagation: FP32 rounding of the differences dz, dh (about 1e-7 of each
     # connection's term), summed over ~200 terms of magnitude <= 2|J| exp(Re d)
-    ("j1j2_6x6_ffnn", 40, "split_bf16_exact", 2e-6),
-    ("j1j2_10x10_ffnn5", 24, "split_bf16_exact", 2e-6),
-    ("j1j2_10x10_ffnn256", 8, "split_bf16_exact", 2e-6),
+    ("j1j2_6x6_ffnn", 40, "split_bf16_exact/diff32", ELOC_SPLIT_BAR),
+    ("j1j2_10x10_ffnn5", 24, "split_bf16_exact/diff32", ELOC_SPLIT_BAR),
+    ("j1j2_10x10_ffnn256", 8, "split_bf16_exact/diff32", ELOC_SPLIT_BAR),
+    ("j1j2_6x6_ffnn", 40, "fp64/diff32", ELOC_SPLIT_BAR),
 ])
 def test_local_energy(name, ns, prec, tol):
     w = W.make_workload(name, ns)
     model, theta, x, ham = dev_inputs(w)
-    el = nq().nqs_local_energy(model, theta, x, ham, prec).cpu().numpy()
+    prec, _, opt = prec.partition("/")
+    el = nq().nqs_local_energy(model, theta, x, ham, prec, diff32=opt == "diff32").cpu().numpy()
     ref = oracle.hamiltonian.local_energy(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.c, w.sign_rule)
     assert np.max(np.abs(el - ref) / np.maximum(np.abs(ref), 1.0)) < tol
 
 
 @pytest.mark.parametrize("name,ns", [("j1j2_6x6_ffnn", 64), ("j1j2_10x10_ffnn5", 32)])
 def test_local_energy_difference_fallback_path(name, ns):
-    """With every connection sent to the FP64-class kernel (test hook), the split-precision
+    """With every connection sent to the FP64-class kernel (test hook), the difference-propagation
     local energies are bit-identical to those of NQS_FP64: the listed connections take exactly
     the FP64 arithmetic and are summed in the same order."""
     w = W.make_workload(name, ns)
@@ -93,11 +96,11 @@ def test_local_energy_difference_fallback_path(name, ns):
     ref = m.nqs_local_energy(model, theta, x, ham, "fp64")
     try:
         m.set_eloc_fallback_all(True)
-        el = m.nqs_local_energy(model, theta, x, ham, "split_bf16_exact")
+        el = m.nqs_local_energy(model, theta, x, ham, "split_bf16_exact", diff32=True)
     finally:
         m.set_eloc_fallback_all(False)
     assert torch.equal(el, ref)
-    el_dp = m.nqs_local_energy(model, theta, x, ham, "split_bf16_exact")
+    el_dp = m.nqs_local_energy(model, theta, x, ham, "split_bf16_exact", diff32=True)
     assert not torch.equal(el_dp, ref)  # the FP32 path ran (it rounds differently)
 
 
@@ -373,7 +376,8 @@ def _golden(name):
     ("j1j2_6x6_ffnn", "fp32", "mixed", 1e-4),
     ("j1j2_10x10_ffnn5", "split_bf16_exact", "mixed", 1e-6),
     ("j1j2_10x10_ffnn5", "split_bf16_exact", "fp64", 1e-6),
-    ("j1j2_10x10_ffnn5", "split_bf16_exact/eloc_fp64", "mixed", 1e-6),
+    ("j1j2_10x10_ffnn5", "split_bf16_exact/diff32", "mixed", 1e-6),
+    ("j1j2_6x6_ffnn", "split_bf16_exact/diff32", "mixed", 1e-6),
 ])
 def test_fullsize_against_oracle(name, prec, solver, tol):
     """Full-size workloads (6x6: FFNN 36-64-64-1, 4096 samples; 10x10: FFNN 100-64x4-1,
@@ -382,19 +386,17 @@ def test_fullsize_against_oracle(name, prec, solver, tol):
     w = W.make_workload(name)
     model, theta, x, ham = dev_inputs(w)
     prec, _, opt = prec.partition("/")
-    eloc_fp64 = opt == "eloc_fp64"
+    diff32 = opt == "diff32"
     dth, em, _, nk = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, prec,
-                                  solver=solver, want_evals=False, eloc_fp64=eloc_fp64)
+                                  solver=solver, want_evals=False, eloc_diff32=diff32)
     assert rel(dth.cpu().numpy(), g["dtheta"]) < tol
-    # <E>: 1e-12 with FP64-class local energies; the FP32 difference propagation's per-sample
-    # errors (<= 2e-6 of max(|E_loc|, 1)) average over the samples
-    etol = 1e-7 if prec == "fp32" else (1e-12 if prec == "fp64" or eloc_fp64 else 1e-8)
+    etol = 1e-7 if prec == "fp32" else emean_bar(w.configs.shape[0], diff32)
     assert abs(em.cpu().numpy()[0] - g["e_mean"]) < etol * abs(g["e_mean"])
     assert np.array_equal(nk.cpu().numpy(), g["n_kept"])
-    if prec.startswith("split") and not eloc_fp64:
-        el = nq().nqs_local_energy(model, theta, x, ham, prec).cpu().numpy()
+    if diff32:
+        el = nq().nqs_local_energy(model, theta, x, ham, prec, diff32=True).cpu().numpy()
         ref = g["eloc"]
-        assert np.max(np.abs(el[g["eloc_idx"]] - ref) / np.maximum(np.abs(ref), 1.0)) < 2e-6
+        assert np.max(np.abs(el[g["eloc_idx"]] - ref) / np.maximum(np.abs(ref), 1.0)) < ELOC_SPLIT_BAR
     # FP64 local energies at full size: the same 1e-12 bar (relative to max(|E_loc|, 1)) as
     # the small cases
     el = nq().nqs_local_energy(model, theta, x, ham, "fp64").cpu().numpy()
