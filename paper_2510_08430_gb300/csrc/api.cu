@@ -211,7 +211,8 @@ void plan_build(Arena& a, long long ns, long long np, int prec, BuildBufs* b) {
     b->means = static_cast<c128*>(a.take(16 * (np + 1)));
     b->ldk = round_up(ns, 64);
     const int nsp = nsplit_of(prec);
-    for (int i = 0; i < 5; ++i) b->planes[i] = i < nsp ? a.take(2ull * 2 * np * b->ldk) : nullptr;
+    for (int i = 0; i < 5; ++i)
+        b->planes[i] = i < plane_units(nsp) ? a.take(2ull * 2 * np * plane_row_len(nsp, i, b->ldk)) : nullptr;
     b->diag = nsp ? static_cast<double*>(a.take(8 * np)) : nullptr;
     b->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(b->ldk / GRAM_GROUP) * np)) : nullptr;
 }
@@ -383,7 +384,8 @@ void plan_wide(Arena& a, const ModelDesc& md, long long ns, int nbonds, const in
     const int nsp = nsplit_of(prec);
     w->ldk = round_up(ns, 64);
     const long long nn = wp.nar_np > 0 ? wp.nar_np : 1;
-    for (int q = 0; q < 5; ++q) w->planes[q] = q < nsp ? a.take(2ull * 2 * nn * w->ldk) : nullptr;
+    for (int q = 0; q < 5; ++q)
+        w->planes[q] = q < plane_units(nsp) ? a.take(2ull * 2 * nn * plane_row_len(nsp, q, w->ldk)) : nullptr;
     w->diag = nsp ? static_cast<double*>(a.take(8 * nn)) : nullptr;
     w->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(w->ldk / GRAM_GROUP) * nn)) : nullptr;
     long long sq = 0;
@@ -397,7 +399,8 @@ void plan_wide(Arena& a, const ModelDesc& md, long long ns, int nbonds, const in
     w->nkn = static_cast<int32_t*>(a.take(4 * MAXB));
     w->ldkT = round_up(wp.max_wide, 64);
     w->ldy = round_up(wp.max_wide, 32);
-    for (int q = 0; q < 5; ++q) w->planesT[q] = q < nsp ? a.take(2ull * 2 * ns * w->ldkT) : nullptr;
+    for (int q = 0; q < 5; ++q)
+        w->planesT[q] = q < plane_units(nsp) ? a.take(2ull * 2 * ns * plane_row_len(nsp, q, w->ldkT)) : nullptr;
     w->gexpT = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(w->ldkT / GRAM_GROUP) * ns)) : nullptr;
     w->diagT = nsp ? static_cast<double*>(a.take(8 * ns)) : nullptr;
     w->Y = nsp ? nullptr : a.take(16 * (size_t)ns * (size_t)w->ldy);
@@ -451,7 +454,8 @@ int run_step_wide(const ModelDesc& md, const HamDesc& hd, const void* theta, con
         const int b = wp.nar[i];
         const long long n = off[b + 1] - off[b], r0 = wp.nar_off[i];
         void* pl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-        for (int q = 0; q < nsp; ++q) pl[q] = static_cast<__nv_bfloat16*>(w.planes[q]) + 2 * r0 * w.ldk;
+        for (int q = 0; q < plane_units(nsp); ++q)
+            pl[q] = static_cast<__nv_bfloat16*>(w.planes[q]) + 2 * r0 * plane_row_len(nsp, q, w.ldk);
         CK(launch_center(prec, nsp, Ob + cs * (size_t)off[b] * (size_t)w.ldo, w.ldo, ns, n, nullptr, w.e,
                          w.F + off[b], nullptr, nsp ? pl : nullptr, w.ldk, nsp ? w.diag + r0 : nullptr,
                          nsp == 5 ? w.gexp + r0 : nullptr, wp.nar_np, status, st),
@@ -1204,7 +1208,8 @@ void plan_batch_bufs(Arena& a, const BatchPlan& bp, int prec, BatchBufs* bb) {
     bb->F = static_cast<c128*>(a.take(16 * (size_t)bp.np_tot));
     bb->S = static_cast<c128*>(a.take(16 * (size_t)bp.sq_tot));
     const int nsp = nsplit_of(prec);
-    for (int q = 0; q < 5; ++q) bb->planes[q] = q < nsp ? a.take(2ull * 2 * bp.np_tot * bp.ldk) : nullptr;
+    for (int q = 0; q < 5; ++q)
+        bb->planes[q] = q < plane_units(nsp) ? a.take(2ull * 2 * bp.np_tot * plane_row_len(nsp, q, bp.ldk)) : nullptr;
     bb->diag = nsp ? static_cast<double*>(a.take(8 * (size_t)bp.np_tot)) : nullptr;
     bb->gexp = nsp == 5 ? static_cast<int8_t*>(a.take((size_t)(bp.ldk / GRAM_GROUP) * bp.np_tot)) : nullptr;
 }
@@ -1293,8 +1298,8 @@ extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const vo
         if (!rc) {
             cudaError_t err = launch_emean(eloc, nullptr, ns, static_cast<c128*>(Emean_out) + i, e, status, st);
             void* pl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-            for (int q = 0; q < nsp; ++q)
-                pl[q] = static_cast<__nv_bfloat16*>(bb.planes[q]) + 2 * po * bp->ldk;
+            for (int q = 0; q < plane_units(nsp); ++q)
+                pl[q] = static_cast<__nv_bfloat16*>(bb.planes[q]) + 2 * po * plane_row_len(nsp, q, bp->ldk);
             if (err == cudaSuccess)
                 err = launch_center(precision, nsp, O, ldo, ns, md.n_p, nullptr, e, bb.F + po, nullptr,
                                     nsp ? pl : nullptr, bp->ldk, nsp ? bb.diag + po : nullptr,

@@ -276,14 +276,31 @@ __device__ __forceinline__ void digits5(long long N, int (&d)[5]) {
 }
 constexpr int GROUP = GRAM_GROUP;  // samples per exponent group: one warp, one sample per lane
 static_assert(GROUP == 32, "one warp per exponent group");
+// The five slices (integers of at most 8 bits scaled by 2^-7, 2^-15, ..., 2^-39) of column c
+// of real rows r (Re) and r + 1 (Im) into the three plane units: slices 1-2 and 3-4 in rows
+// of 2 ldk (column 64 (c / 32) + 32 h + c % 32 for the pair's slice h), slice 5 in rows of ldk.
+__device__ __forceinline__ void store_slices(__nv_bfloat16* __restrict__ p12, __nv_bfloat16* __restrict__ p34,
+                                             __nv_bfloat16* __restrict__ p5, long long r, long long c, long long ldk,
+                                             const int (&dr5)[5], const int (&di5)[5]) {
+    const float qs[5] = {0x1p-7f, 0x1p-15f, 0x1p-23f, 0x1p-31f, 0x1p-39f};
+    const long long cp = 64 * (c / GROUP) + (c % GROUP);
+    __nv_bfloat16* u[2] = {p12, p34};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __nv_bfloat16* b = u[q >> 1] + 32 * (q & 1) + cp;
+        b[r * 2 * ldk] = __float2bfloat16_rn((float)dr5[q] * qs[q]);
+        b[(r + 1) * 2 * ldk] = __float2bfloat16_rn((float)di5[q] * qs[q]);
+    }
+    p5[r * ldk + c] = __float2bfloat16_rn((float)dr5[4] * qs[4]);
+    p5[(r + 1) * ldk + c] = __float2bfloat16_rn((float)di5[4] * qs[4]);
+}
+
 __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restrict__ O, long long ldo, long long ns,
                                                             const double* __restrict__ w,
                                                             const c128* __restrict__ e, c128* __restrict__ F,
-                                                            c128* __restrict__ Omean, __nv_bfloat16* __restrict__ pl0,
-                                                            __nv_bfloat16* __restrict__ pl1,
-                                                            __nv_bfloat16* __restrict__ pl2,
-                                                            __nv_bfloat16* __restrict__ pl3,
-                                                            __nv_bfloat16* __restrict__ pl4, int8_t* __restrict__ gexp,
+                                                            c128* __restrict__ Omean, __nv_bfloat16* __restrict__ p12,
+                                                            __nv_bfloat16* __restrict__ p34,
+                                                            __nv_bfloat16* __restrict__ p5, int8_t* __restrict__ gexp,
                                                             long long gstride, long long ldk, double* __restrict__ diag,
                                                             ShardArgs sa, DevStatus* status) {
     __shared__ double sh[32];
@@ -309,7 +326,6 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         mi = sa.mean_in[p].im;
     }
     double fr = 0.0, fi = 0.0, dg = 0.0;
-    __nv_bfloat16* pls[5] = {pl0, pl1, pl2, pl3, pl4};
     const int lane = threadIdx.x & 31;
     // blockDim.x is a multiple of 32 and ldk of GROUP: the samples of a group are one warp
     for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
@@ -341,12 +357,7 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         int dr5[5], di5[5];
         digits5(__double2ll_rn(dr * sc), dr5);
         digits5(__double2ll_rn(di * sc), di5);
-        const float qs[5] = {0x1p-7f, 0x1p-15f, 0x1p-23f, 0x1p-31f, 0x1p-39f};
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            pls[q][(2 * p) * ldk + s] = __float2bfloat16_rn((float)dr5[q] * qs[q]);
-            pls[q][(2 * p + 1) * ldk + s] = __float2bfloat16_rn((float)di5[q] * qs[q]);
-        }
+        store_slices(p12, p34, p5, 2 * p, s, ldk, dr5, di5);
     }
     fr = block_sum(fr, sh);
     fi = block_sum(fi, sh);
@@ -369,11 +380,9 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
 // One CTA per 32 x 32 (parameter, sample) tile; warp w takes samples w, w + 8, w + 16, w + 24
 // of the tile, lane r its parameter k0 + r.
 __global__ void __launch_bounds__(256) transpose_group_kernel(const c128* __restrict__ dO, long long ldo, long long ns,
-                                                               long long nb, __nv_bfloat16* __restrict__ pl0,
-                                                               __nv_bfloat16* __restrict__ pl1,
-                                                               __nv_bfloat16* __restrict__ pl2,
-                                                               __nv_bfloat16* __restrict__ pl3,
-                                                               __nv_bfloat16* __restrict__ pl4,
+                                                               long long nb, __nv_bfloat16* __restrict__ p12,
+                                                               __nv_bfloat16* __restrict__ p34,
+                                                               __nv_bfloat16* __restrict__ p5,
                                                                int8_t* __restrict__ gexp, long long ldk,
                                                                double* __restrict__ diag) {
     __shared__ c128 t[32][33];
@@ -384,7 +393,6 @@ __global__ void __launch_bounds__(256) transpose_group_kernel(const c128* __rest
         t[r][lane] = (k < nb && s < ns) ? dO[k * ldo + s] : mk<double>(0.0, 0.0);
     }
     __syncthreads();
-    __nv_bfloat16* pls[5] = {pl0, pl1, pl2, pl3, pl4};
     const double inv_ns = 1.0 / (double)ns;
     for (int c = wid; c < 32; c += 8) {
         const long long s = s0 + c;
@@ -409,15 +417,8 @@ __global__ void __launch_bounds__(256) transpose_group_kernel(const c128* __rest
         int dr5[5], di5[5];
         digits5(__double2ll_rn(dr * sc), dr5);
         digits5(__double2ll_rn(di * sc), di5);
-        const float qs[5] = {0x1p-7f, 0x1p-15f, 0x1p-23f, 0x1p-31f, 0x1p-39f};
         const long long k = k0 + lane;
-        if (k < ldk) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                pls[q][(2 * s) * ldk + k] = __float2bfloat16_rn((float)dr5[q] * qs[q]);
-                pls[q][(2 * s + 1) * ldk + k] = __float2bfloat16_rn((float)di5[q] * qs[q]);
-            }
-        }
+        if (k < ldk) store_slices(p12, p34, p5, 2 * s, k, ldk, dr5, di5);
     }
 }
 
@@ -428,8 +429,7 @@ cudaError_t launch_transpose_group(const c128* dO, long long ldo, long long ns, 
     const dim3 grid((unsigned)((ns + 31) / 32), (unsigned)(ldk / 32));
     count_launch();
     transpose_group_kernel<<<grid, 256, 0, st>>>(dO, ldo, ns, nb, (__nv_bfloat16*)planes[0], (__nv_bfloat16*)planes[1],
-                                                 (__nv_bfloat16*)planes[2], (__nv_bfloat16*)planes[3],
-                                                 (__nv_bfloat16*)planes[4], gexp, ldk, diag);
+                                                 (__nv_bfloat16*)planes[2], gexp, ldk, diag);
     return cudaGetLastError();
 }
 
@@ -469,8 +469,7 @@ cudaError_t launch_center(int prec, int nsplit, void* O, long long ldo, long lon
         count_launch();
         center_group_kernel<<<grid, 256, 0, st>>>((const c128*)O, ldo, ns, w, e, F, Omean,
                                                   (__nv_bfloat16*)planes[0], (__nv_bfloat16*)planes[1],
-                                                  (__nv_bfloat16*)planes[2], (__nv_bfloat16*)planes[3],
-                                                  (__nv_bfloat16*)planes[4], gexp, gstride, ldk, diag, sa, status);
+                                                  (__nv_bfloat16*)planes[2], gexp, gstride, ldk, diag, sa, status);
     } else if (nsplit == 2 || nsplit == 3) {
         __nv_bfloat16* p0 = (__nv_bfloat16*)planes[0];
         __nv_bfloat16* p1 = (__nv_bfloat16*)planes[1];

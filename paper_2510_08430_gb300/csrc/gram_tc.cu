@@ -143,6 +143,20 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory descriptor of slice `pl` at MMA K-step kk within one operand's part of a stage.
+// Element-wise splits (PAIRED false): pl-th tile of 128 rows x KB BF16. Grouped split (PAIRED):
+// a 16 KB tile of 128-byte rows holding slices 1-2 (32 samples each, 128-byte swizzle), one
+// holding slices 3-4, and an 8 KB tile of slice 5 (64-byte rows, 64-byte swizzle); a slice's
+// K-steps start 32 bytes apart inside its half of the row.
+template <bool PAIRED, int KB>
+__device__ __forceinline__ uint64_t plane_desc(uint32_t side, int pl, int kk) {
+    if (PAIRED) {
+        if (pl < 4) return sdesc<64>(side + (uint32_t)((pl >> 1) * (BM * 128) + (pl & 1) * 64 + kk * 32));
+        return sdesc<32>(side + (uint32_t)(2 * BM * 128 + kk * 32));
+    }
+    return sdesc<KB>(side + (uint32_t)(pl * (BM * KB * 2) + kk * 32));
+}
+
 // Instruction descriptor, kind::f16: D FP32, A/B BF16, both K-major, M = 128, N = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
@@ -305,7 +319,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            for (int p = 0; p < NS; ++p) asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.m[p]) : "memory");
+            for (int p = 0; p < (GROUPED ? 3 : NS); ++p)
+                asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.m[p]) : "memory");
             uint32_t q = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
@@ -320,11 +335,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (!mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) { ok = false; break; }
                     unsigned char* st = ring + (size_t)s * STAGE_BYTES;
                     mbar_expect_tx(&full_bar[s], (diag ? NS : 2 * NS) * KTILE_BYTES);
-                    for (int p = 0; p < NS; ++p)
-                        tma_load_2d(st + p * KTILE_BYTES, &maps.m[p], &full_bar[s], kb * KB, rowA);
-                    if (!diag)
+                    if (GROUPED) {  // three boxes per operand: slices 1-2, 3-4 (128-byte rows), 5
+                        for (int o = 0; o < (diag ? 1 : 2); ++o) {
+                            unsigned char* side = st + o * NS * KTILE_BYTES;
+                            const int row = o ? rowB : rowA;
+                            tma_load_2d(side, &maps.m[0], &full_bar[s], kb * 2 * KB, row);
+                            tma_load_2d(side + BM * 128, &maps.m[1], &full_bar[s], kb * 2 * KB, row);
+                            tma_load_2d(side + 2 * BM * 128, &maps.m[2], &full_bar[s], kb * KB, row);
+                        }
+                    } else {
                         for (int p = 0; p < NS; ++p)
-                            tma_load_2d(st + (NS + p) * KTILE_BYTES, &maps.m[p], &full_bar[s], kb * KB, rowB);
+                            tma_load_2d(st + p * KTILE_BYTES, &maps.m[p], &full_bar[s], kb * KB, rowA);
+                        if (!diag)
+                            for (int p = 0; p < NS; ++p)
+                                tma_load_2d(st + (NS + p) * KTILE_BYTES, &maps.m[p], &full_bar[s], kb * KB, rowB);
+                    }
                 }
             }
             if (!ok) {
@@ -366,12 +391,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int pr = 0; pr < SP::NPROD; ++pr) {
                             for (int kk = sub * kpi; kk < (sub + 1) * kpi; ++kk) {
-                                const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes inside the swizzle row
-                                const uint32_t aad = base + SP::pa(pr) * KTILE_BYTES + off;
-                                const uint32_t bad = base + boff + SP::pb(pr) * KTILE_BYTES + off;
+                                // 16 BF16 = 32 bytes per K-step inside the swizzle row
+                                const uint64_t ad = plane_desc<GROUPED, KB>(base, SP::pa(pr), kk);
+                                const uint64_t bd = plane_desc<GROUPED, KB>(base + boff, SP::pb(pr), kk);
                                 // product 0 -> A0; products 1.. -> A1; the first write of each resets it
                                 const uint32_t first = (kk == sub * kpi && pr <= 1) ? 0u : 1u;
-                                umma(tmem_d + (pr == 0 ? 0u : 128u), sdesc<KB>(aad), sdesc<KB>(bad), idesc, first);
+                                umma(tmem_d + (pr == 0 ? 0u : 128u), ad, bd, idesc, first);
                             }
                         }
                         umma_commit(&tfull_bar[acc]);   // hands the accumulator pair to the epilogue
@@ -602,9 +627,13 @@ cudaError_t launch_gram_tc_tab(int nsplit, const void* const* planes, const int8
     if (ldk % tc::BK != 0 || kpad % tc::BK != 0 || kpad > ldk) return cudaErrorInvalidValue;
     const int kb = nsplit == 5 ? 32 : 64;
     tc::Maps maps;
-    for (int p = 0; p < nsplit; ++p) {
+    for (int p = 0; p < plane_units(nsplit); ++p) {
         if (reinterpret_cast<uintptr_t>(planes[p]) & 15) return cudaErrorInvalidValue;
-        if (!make_map(&maps.m[p], planes[p], rows, ldk, kb)) return cudaErrorInvalidValue;
+        // grouped split: units of slices 1-2 and 3-4 have rows of 2 ldk read in 64-element
+        // (128-byte) boxes; slice 5 rows of ldk in 32-element boxes
+        const long long len = plane_row_len(nsplit, p, ldk);
+        const int box = (nsplit == 5 && p < 2) ? 64 : kb;
+        if (!make_map(&maps.m[p], planes[p], rows, len, box)) return cudaErrorInvalidValue;
     }
     if (nsplit == 2) return launch_tc<2, false, 64>(maps, tab, kpad, kpi, scale, nullptr, np, S, status, sms, st);
     if (nsplit == 3) return launch_tc<3, false, 64>(maps, tab, kpad, kpi, scale, nullptr, np, S, status, sms, st);

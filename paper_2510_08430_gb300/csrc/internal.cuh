@@ -88,7 +88,8 @@ cudaError_t launch_emean(const c128* eloc, const double* w, long long ns, c128* 
 // nsplit 0: dO written in place (prec FP64/FP32); nsplit 2 or 3: element-wise BF16
 // split planes of dO (O is c128, unchanged)
 // (split modes also write diag[k] = sum_s w_s |dO_k(s)|^2 in FP64; nsplit 5 = grouped
-// error-free split with int8 exponents gexp[group][param], groups of GRAM_GROUP samples)
+// error-free split with int8 exponents gexp[group][param], groups of GRAM_GROUP samples,
+// stored as three plane units, see plane_units)
 cudaError_t launch_shard_sums(int prec, const void* O, long long ldo, long long ns, long long np, const c128* eloc,
                               c128* osum, c128* esum, cudaStream_t st);
 cudaError_t launch_ecenter(const c128* eloc, long long ns, const c128* emean, c128* e, cudaStream_t st);
@@ -137,6 +138,15 @@ cudaError_t launch_gram_simt(int prec, const void* dO, long long ldo, long long 
                              double scale, const GramTable& tab, c128* S, cudaStream_t st);
 constexpr int GRAM_KPI_DEFAULT = 4;    // MMA K-steps (16 samples) per accumulator flush
 constexpr int GRAM_GROUP = 32;         // samples per exponent group of the grouped split (gexp rows)
+// Storage of the split planes: nsplit arrays of 2 np rows x ldk BF16 for the element-wise
+// splits; for the grouped five-slice split three units: slices 1-2 and slices 3-4 each share
+// rows of 2 ldk (group g of slice 2u + h at columns 64 g + 32 h .. + 31, so that one 128-byte
+// row of the tensor-core Gram's TMA boxes carries two slices of a group), slice 5 alone in
+// rows of ldk.
+inline int plane_units(int nsplit) { return nsplit == 5 ? 3 : nsplit; }
+inline long long plane_row_len(int nsplit, int unit, long long ldk) {
+    return (nsplit == 5 && unit < 2) ? 2 * ldk : ldk;
+}
 // tcgen05 Gram over nsplit element-wise BF16 split planes (2: 3 products; 3: 6 products),
 // FP32 accumulation per 64-sample K block folded into double-float sums;
 // cudaErrorNotSupported off sm_103.
