@@ -95,6 +95,13 @@ def zero_sz_configs(n_sites: int, n_samples: int, rng: np.random.Generator) -> n
     return out
 
 
+def metropolis_uniforms(n_steps: int, n_chains: int, seed: int) -> np.ndarray:
+    """float64 [n_steps, n_chains, 3] uniform draws in [0, 1) for the exchange-move sampler
+    (per step and chain: which up spin, which down spin, acceptance), from
+    ``numpy.random.default_rng(seed)``."""
+    return np.random.default_rng(seed).random((n_steps, n_chains, 3))
+
+
 def chain_bonds(n: int, j: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
     """Periodic chain: bonds (i, i+1 mod n). Returns (int32 [nb,2], float64 [nb])."""
     if n < 3:
@@ -158,6 +165,8 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
       splits cannot reach a 1e-6 relative dtheta error on this workload).
     * ``j1j2_10x10_ffnn256`` FFNN 100-256-256-1, 10x10 J1-J2, 32768 samples.
     * ``batch8x8_<i>``     instance i (0..15) of the batched 8x8 workload.
+    * ``chain16_rbm``      RBM alpha=2 on the 16-site Heisenberg chain (the chain of Table 2),
+      Marshall sign rule, 1024 samples, FP64: the starting point of the VMC training loop.
     The last two also use the five-slice split: the two-slice (hi + lo) split misses the
     1e-6 dtheta bar by orders of magnitude on these lattices.
     """
@@ -195,6 +204,16 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
         ij, jj = square_j1j2_bonds(10, 10, 1.0, 0.5)
         return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
                         1e-3, 1e-10, "split_bf16_exact")
+    if name == "chain16_rbm":
+        model = Model(RBM, (16, 32))
+        theta = init_params(model, np.random.default_rng(20))
+        ns = 1024 if n_samples is None else n_samples
+        configs = zero_sz_configs(16, ns, np.random.default_rng(21))
+        ij, jj = chain_bonds(16, 1.0)
+        # Marshall sign rule: the chain's ground state then has positive amplitudes (same
+        # spectrum); without it the RBM loop stalls near 0.8 of the ground energy
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "fp64", 1.0, -1)
     if name.startswith("batch8x8_"):
         i = int(name.split("_")[1])
         if not 0 <= i < 16:
