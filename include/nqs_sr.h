@@ -198,6 +198,28 @@ NQS_API int nqs_local_energy_ex(const nqs_model* m, const void* theta, const int
                         const nqs_hamiltonian* h, int32_t precision, int32_t flags, void* eloc_out,
                         nqs_workspace* ws, void* stream);
 
+/* ---- variational Monte Carlo loop (Sec. 1: samples of |psi|^2 by Markov chain Monte Carlo;
+ * Sec. 2: the SR update) ----
+ * nqs_metropolis -- n_steps exchange-move Metropolis steps on n_chains independent chains.
+ * Each step gives every chain one proposal: with its uniforms (u1, u2, u3) it picks the k1-th
+ * up spin i, k1 = floor(u1 n_up), and the k2-th down spin j, k2 = floor(u2 n_down) (sites
+ * counted in increasing order), and accepts the exchange x' = x with spins i and j flipped
+ * when u3 < |psi(x') / psi(x)|^2 (FP64 forwards; the ratio is that of the FP64 local energies'
+ * connected configurations). Total S^z of every chain is conserved; the chains sample |psi|^2
+ * in their S^z sector. A chain with no up or no down spin does not move.
+ *   theta    : c128 [n_p] (device).
+ *   configs  : int8 [n_chains][N] (device), updated in place.
+ *   uniforms : float64 [n_steps][n_chains][3] (device) in [0, 1), one triple per step and chain;
+ *              may be NULL when n_steps = 0.
+ *   n_accepted: int64 [1] (device) or NULL: receives the number of accepted moves.
+ * nqs_metropolis_workspace_size gives the workspace it needs.
+ * nqs_theta_update -- theta += dtheta (c128 [n_p], device), the update of one SR step. */
+NQS_API int nqs_metropolis_workspace_size(const nqs_model* m, int64_t n_chains, size_t* bytes);
+NQS_API int nqs_metropolis(const nqs_model* m, const void* theta, int8_t* configs, int64_t n_chains,
+                           int32_t n_steps, const double* uniforms, int64_t* n_accepted, nqs_workspace* ws,
+                           void* stream);
+NQS_API int nqs_theta_update(void* theta, const void* dtheta, int64_t n_p, void* stream);
+
 /* nqs_connections -- the integer work of E_loc: for every sample, the bonds with
  * x_i != x_j in bond order. conn_count: int32 [n_s]; conn_offset: int64 [n_s+1]
  * (exclusive prefix sum); conn_bond: int32 [max_conn] receives the bond indices

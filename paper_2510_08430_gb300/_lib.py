@@ -65,6 +65,9 @@ SIGNATURES = {
     "nqs_jacobian": (C.c_int, [MP, P, P, I64, I32, P, P, I64, P, P]),
     "nqs_local_energy": (C.c_int, [MP, P, P, I64, HP, I32, P, P, P]),
     "nqs_local_energy_ex": (C.c_int, [MP, P, P, I64, HP, I32, I32, P, P, P]),
+    "nqs_metropolis_workspace_size": (C.c_int, [MP, I64, SZ]),
+    "nqs_metropolis": (C.c_int, [MP, P, P, I64, I32, P, P, P, P]),
+    "nqs_theta_update": (C.c_int, [P, P, I64, P]),
     "nqs_connections": (C.c_int, [P, I64, HP, P, P, P, I64, C.POINTER(C.c_int64), P, P]),
     "nqs_vjp": (C.c_int, [P, I64, I64, I64, I32, P, P, P]),
     "ntk_solve_workspace_size": (C.c_int, [I64, I64, I32, SZ]),

@@ -488,6 +488,65 @@ def set_limits(max_sweeps: int = 0, wait_ns: int = 0) -> None:
     check(_lib.load().nqs_set_limits(int(max_sweeps), int(wait_ns)))
 
 
+def metropolis(model: Model, theta: torch.Tensor, configs: torch.Tensor, uniforms: torch.Tensor,
+               ws: Optional[Workspace] = None, count: bool = True) -> Optional[int]:
+    """nqs_metropolis: uniforms.shape[0] exchange-move Metropolis steps on every chain (rows of
+    configs, int8, updated in place). uniforms: float64 [n_steps, n_chains, 3] on the device.
+    Returns the number of accepted moves (count=True; this synchronises) or None."""
+    lib = _lib.load()
+    n = int(configs.shape[0])
+    steps = int(uniforms.shape[0])
+    if tuple(uniforms.shape) != (steps, n, 3) or uniforms.dtype != torch.float64:
+        raise ValueError("uniforms must be float64 [n_steps, n_chains, 3]")
+    ws = ws or Workspace()
+    ws.ensure(_size(lib.nqs_metropolis_workspace_size, C.byref(model.c), n))
+    acc = torch.zeros(1, dtype=torch.int64, device=configs.device) if count else None
+    u = uniforms.contiguous()
+    with _on(theta, configs, u):
+        check(lib.nqs_metropolis(C.byref(model.c), _ptr(theta), _ptr(configs), n, steps, _ptr(u), _ptr(acc), ws.h,
+                                 _stream()))
+    return int(acc.item()) if count else None
+
+
+def theta_update(theta: torch.Tensor, dtheta: torch.Tensor) -> None:
+    """theta += dtheta in place (nqs_theta_update; c128 device vectors)."""
+    with _on(theta, dtheta):
+        check(_lib.load().nqs_theta_update(_ptr(theta), _ptr(dtheta), int(theta.numel()), _stream()))
+
+
+def vmc_train(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamiltonian, block_off,
+              n_iter: int, n_steps: int, diag_shift: float, cutoff: float, eta: float, precision="fp64",
+              solver="fp64", uniforms=None, generator: Optional[torch.Generator] = None) -> dict:
+    """The VMC loop on the device: per iteration n_steps Metropolis steps of every chain
+    (nqs_metropolis), one block-layer SR step on the chains' configurations (sr_step with the
+    given blocks; one block [0, n_p] is the full QGT) and theta += dtheta (nqs_theta_update).
+    theta (c128) and configs (int8) are updated in place. uniforms: optional list of n_iter
+    float64 [n_steps, n_chains, 3] device tensors (default: drawn from `generator`). Returns
+    {"energies": <E> per iteration (c128, CPU), "accepted": accepted moves per iteration}."""
+    n = int(configs.shape[0])
+    step = SRStep(model, n, ham, block_off, precision, diag_shift, cutoff, 0, eta, solver=solver,
+                  device=configs.device)
+    ws = Workspace()
+    emeans = torch.empty(n_iter, dtype=torch.complex128, device=configs.device)
+    accepted = torch.zeros(n_iter, dtype=torch.int64, device=configs.device)
+    lib = _lib.load()
+    ws.ensure(_size(lib.nqs_metropolis_workspace_size, C.byref(model.c), n))
+    for it in range(n_iter):
+        u = uniforms[it] if uniforms is not None else torch.rand(
+            (n_steps, n, 3), dtype=torch.float64, device=configs.device, generator=generator)
+        u = u.contiguous()
+        acc = accepted[it:it + 1]
+        with _on(theta, configs, u):
+            check(lib.nqs_metropolis(C.byref(model.c), _ptr(theta), _ptr(configs), n, int(u.shape[0]), _ptr(u),
+                                     _ptr(acc), ws.h, _stream()))
+        dth, em = step(theta, configs)
+        emeans[it:it + 1].copy_(em)
+        theta_update(theta, dth)
+    step.ws.sync_status()
+    ws.sync_status()
+    return {"energies": emeans.cpu().numpy(), "accepted": accepted.cpu().numpy()}
+
+
 def set_eloc_fallback_all(on: bool) -> None:
     """Test hook (nqs_set_eloc_fallback_all): every connection of the FP32 difference-propagation
     local energies goes to the FP64-class kernel that otherwise takes only the connections FP32

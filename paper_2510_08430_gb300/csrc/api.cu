@@ -293,6 +293,29 @@ int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, 
     return NQS_OK;
 }
 
+// exchange-move sampler: FP64 forward of the chains, the proposals as a bond table, the
+// FP64 connected forwards' ratios
+struct McBufs {
+    JacBufs jb;
+    void* wdf;
+    int32_t *pairs, *valid, *csamp, *cbond;
+    double* bond_J;
+    long long* nconn;
+    c128* ratio;
+};
+void plan_mc(Arena& a, const ModelDesc& md, long long n, McBufs* b) {
+    plan_model(a, md, n, NQS_FP64, &b->jb, false);
+    const long long we = model_wt_elems(md);
+    b->wdf = a.take(16 * (size_t)(we > 0 ? we : 1));
+    b->pairs = static_cast<int32_t*>(a.take(8 * (size_t)n));
+    b->valid = static_cast<int32_t*>(a.take(4 * (size_t)n));
+    b->csamp = static_cast<int32_t*>(a.take(4 * (size_t)n));
+    b->cbond = static_cast<int32_t*>(a.take(4 * (size_t)n));
+    b->bond_J = static_cast<double*>(a.take(8 * (size_t)n));
+    b->nconn = static_cast<long long*>(a.take(8));
+    b->ratio = static_cast<c128*>(a.take(16 * (size_t)n));
+}
+
 int check_ws(nqs_workspace* ws, const Arena& need) {
     if (!ws) return fail(NQS_ERR_INVALID_ARG, "workspace is NULL");
     const size_t total = need.used + STATUS_BYTES;
@@ -847,6 +870,63 @@ int nqs_local_energy_ex(const nqs_model* m, const void* theta, const int8_t* con
     if (rc) return rc;
     return run_eloc(md, rp, hd, configs, n_s, jb, eb, static_cast<c128*>(eloc_out), status_of(ws), st,
                     eloc_dp(precision, flags));
+}
+
+int nqs_metropolis_workspace_size(const nqs_model* m, int64_t n_chains, size_t* bytes) {
+    ModelDesc md;
+    if (!bytes || n_chains < 1) return fail(NQS_ERR_INVALID_ARG, "nqs_metropolis_workspace_size: bad arguments");
+    if (build_model_desc(m, n_chains, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    Arena a = sizing_arena();
+    McBufs b;
+    plan_mc(a, md, n_chains, &b);
+    *bytes = a.used + STATUS_BYTES;
+    return NQS_OK;
+}
+
+int nqs_metropolis(const nqs_model* m, const void* theta, int8_t* configs, int64_t n_chains, int32_t n_steps,
+                   const double* uniforms, int64_t* n_accepted, nqs_workspace* ws, void* stream) {
+    ModelDesc md;
+    if (n_chains < 1 || n_steps < 0 || !theta || !configs || (n_steps > 0 && !uniforms))
+        return fail(NQS_ERR_INVALID_ARG, "nqs_metropolis: bad arguments");
+    if (build_model_desc(m, n_chains, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (n_chains > 2147483647LL) return fail(NQS_ERR_INVALID_ARG, "nqs_metropolis: more than 2^31 - 1 chains");
+    Arena a = arena_of(ws);
+    McBufs b;
+    plan_mc(a, md, n_chains, &b);
+    int rc = check_ws(ws, a);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(n_accepted);
+    if (acc) CK(cudaMemsetAsync(acc, 0, sizeof(*acc), st), "memset");
+    if (n_steps == 0) return NQS_OK;
+    CK(launch_prepare_params(NQS_FP64, md, theta, b.jb.thR, b.jb.wtR, st), "prepare_params");
+    CK(launch_split_weights(md, b.jb.wtR, b.wdf, st), "split_weights");
+    CK(launch_mc_setup(n_chains, b.bond_J, b.csamp, b.cbond, b.nconn, st), "mc_setup");
+    HamDesc hd;
+    hd.n_sites = md.N;
+    hd.n_bonds = (int)n_chains;
+    hd.bond_ij = b.pairs;
+    hd.bond_J = b.bond_J;
+    hd.c = 1.0;
+    hd.sign_rule = 1;
+    for (int t = 0; t < n_steps; ++t) {
+        const double* u = uniforms + (size_t)3 * (size_t)n_chains * (size_t)t;
+        CK(launch_forward(NQS_FP64, md, b.jb.thR, b.jb.wtR, configs, n_chains, b.jb.Z, b.jb.logpsi, st), "forward");
+        CK(launch_mc_propose(configs, md.N, n_chains, u, b.pairs, b.valid, st), "mc_propose");
+        CK(launch_conn_terms(NQS_FP64, md, b.jb.thR, b.jb.wtR, b.wdf, b.jb.Z, b.jb.logpsi, configs, hd, b.cbond,
+                             b.csamp, b.nconn, n_chains, b.ratio, st),
+           "ratios");
+        CK(launch_mc_accept(configs, md.N, n_chains, u, b.pairs, b.valid, b.ratio, acc, st), "mc_accept");
+    }
+    return NQS_OK;
+}
+
+int nqs_theta_update(void* theta, const void* dtheta, int64_t n_p, void* stream) {
+    if (!theta || !dtheta || n_p < 0) return fail(NQS_ERR_INVALID_ARG, "nqs_theta_update: bad arguments");
+    CK(launch_theta_update(static_cast<c128*>(theta), static_cast<const c128*>(dtheta), n_p,
+                           static_cast<cudaStream_t>(stream)),
+       "theta_update");
+    return NQS_OK;
 }
 
 int nqs_connections(const int8_t* configs, int64_t n_s, const nqs_hamiltonian* h, int32_t* conn_count,

@@ -78,6 +78,14 @@ cudaError_t launch_conn_terms_dp(const ModelDesc& md, const void* thR, const voi
                                  const void* Z, const c128* logpsi, const int8_t* x, long long ns, const HamDesc& h,
                                  const int32_t* conn_bond, const int32_t* conn_sample, const long long* nconn_ptr,
                                  long long max_conn, c128* terms, const DpBufs& b, cudaStream_t st);
+// ---- exchange-move Metropolis sampler and parameter update (sampler.cu) ----
+cudaError_t launch_mc_setup(long long n, double* bond_J, int32_t* csamp, int32_t* cbond, long long* nconn,
+                            cudaStream_t st);
+cudaError_t launch_mc_propose(const int8_t* x, int N, long long n, const double* u, int32_t* pairs, int32_t* valid,
+                              cudaStream_t st);
+cudaError_t launch_mc_accept(int8_t* x, int N, long long n, const double* u, const int32_t* pairs,
+                             const int32_t* valid, const c128* ratio, unsigned long long* n_acc, cudaStream_t st);
+cudaError_t launch_theta_update(c128* theta, const c128* dtheta, long long n, cudaStream_t st);
 cudaError_t launch_eloc_reduce(const int8_t* x, long long ns, const HamDesc& h,
                                const long long* off, const c128* terms, c128* eloc,
                                DevStatus* status, cudaStream_t st);

@@ -108,6 +108,13 @@ def test_newer_entry_points_validate_on_the_host(lib):
     assert lib.nqs_local_energy_ex(C.byref(m.c), fake, fake, 8, C.byref(h), 1, _lib.NQS_ELOC_DIFF32, fake, None,
                                    None) == -1
     assert b"NQS_ELOC_DIFF32" in lib.nqs_last_error()
+    # sampler: no chains, negative steps, missing uniforms
+    assert lib.nqs_metropolis(C.byref(m.c), fake, fake, 0, 1, fake, None, None, None) == -1
+    assert lib.nqs_metropolis(C.byref(m.c), fake, fake, 4, -1, fake, None, None, None) == -1
+    assert lib.nqs_metropolis(C.byref(m.c), fake, fake, 4, 3, None, None, None, None) == -1
+    assert lib.nqs_theta_update(None, fake, 4, None) == -1
+    out = C.c_size_t(0)
+    assert lib.nqs_metropolis_workspace_size(C.byref(m.c), 64, C.byref(out)) == 0 and out.value > 0
     # shard sums and VJP: leading dimension below n_s
     assert lib.nqs_shard_sums(fake, 10, 64, 10, 0, fake, fake, fake, None) == -1
     assert lib.nqs_vjp(fake, 10, 64, 10, 0, fake, fake, None) == -1
