@@ -347,6 +347,54 @@ def compare_steps(nq, torch, np, w, model, ham, theta, x, dth, solver) -> dict:
     return out
 
 
+VMC_ITERS, VMC_STEPS = 40, 16
+
+
+def vmc_gpu(nq, torch, np) -> dict:
+    """The device VMC loop (NEXT #3) on the 16-site chain of Table 2: RBM alpha = 2, 1024
+    chains, 16 exchange-move Metropolis steps and one block-layer SR step per iteration. Its
+    energy is set against Table 2's block-layer value (Pauli units)."""
+    import workloads as W
+    w = W.make_workload("chain16_rbm")
+    model = nq.Model.from_workload(w.model)
+    theta = torch.as_tensor(w.theta, device="cuda")
+    x = torch.as_tensor(w.configs, device="cuda")
+    ham = nq.Hamiltonian(w.model.n_sites, w.bond_ij, w.bond_j, w.c, w.sign_rule)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    nq.vmc_train(model, theta.clone(), x.clone(), ham, w.block_off, 2, VMC_STEPS, w.diag_shift, w.cutoff, 0.05,
+                 "fp64", "mixed", generator=g)  # warm-up
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    out = nq.vmc_train(model, theta, x, ham, w.block_off, VMC_ITERS, VMC_STEPS, w.diag_shift, w.cutoff, 0.05,
+                       "fp64", "mixed", generator=g)
+    e.record()
+    e.synchronize()
+    secs = s.elapsed_time(e) / 1e3
+    e_last = float(np.mean(out["energies"][-10:].real))
+    with open(os.path.join(ROOT, "tests", "golden", "paper_values.json")) as f:
+        ref = float(json.load(f)["table2_block_energy"]["value"])
+    return {"workload": f"chain16_rbm: RBM (16, 32), 1024 chains, {VMC_STEPS} Metropolis steps + 1 SR step "
+                        f"per iteration, {VMC_ITERS} iterations from the random start",
+            "seconds_per_iteration": secs / VMC_ITERS, "iterations_per_s": VMC_ITERS / secs,
+            "energy_last10": e_last, "table2_block_energy": ref,
+            "rel_diff_vs_table2": (e_last - ref) / abs(ref),
+            "acceptance": float(out["accepted"][-1]) / (VMC_STEPS * w.n_samples)}
+
+
+def vmc_oracle_sample(n_iter: int = 2) -> dict:
+    """The oracle's VMC loop on the same chain workload: seconds per iteration (bounded sample)."""
+    import oracle
+    import workloads as W
+    w = W.make_workload("chain16_rbm")
+    us = [W.metropolis_uniforms(VMC_STEPS, w.n_samples, 500 + k) for k in range(n_iter)]
+    t0 = time.perf_counter()
+    oracle.vmc.train(w.model, w.theta, w.configs, w.bond_ij, w.bond_j, w.block_off, w.diag_shift, w.cutoff, 0.05,
+                     us, w.c, w.sign_rule)
+    return {"seconds_per_iteration": (time.perf_counter() - t0) / n_iter, "sample": f"{n_iter} iterations"}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank: int, world: int) -> None:
     import workloads as W
@@ -552,6 +600,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         line["graph_replay"] = {"unavailable": str(exc)[:200]}
     if world == 1 and not args.no_fp64_compare:
         line["comparisons"] = compare_steps(nq, torch, np, w, model, ham, theta, x, dth_split, args.solver)
+        try:
+            line["comparisons"]["vmc_chain16"] = vmc_gpu(nq, torch, np)
+        except Exception as exc:
+            line["comparisons"]["vmc_chain16"] = {"unavailable": str(exc)[:200]}
     if world == 1 and not args.no_cpu_baseline:
         info = oracle_sample(w)
         one = oracle_sample_single_thread(w)
@@ -562,7 +614,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                                 "single_thread": ({"value": 1.0 / one["seconds_per_step"], "unit": "steps/s",
                                                    "threads": 1, "sample": one["sample"],
                                                    "stage_seconds": one["stage_seconds"]}
-                                                  if "seconds_per_step" in one else one)}
+                                                  if "seconds_per_step" in one else one),
+                                "vmc_chain16": vmc_oracle_sample()}
     print(json.dumps(line), flush=True)
 
 
