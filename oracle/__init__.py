@@ -18,6 +18,8 @@ Every function follows the paper's definitions directly, in float64/complex128:
                    block-layer paragraph), the full-QGT and NTK comparators.
 * ``exact``        exact expectations by enumeration of all 2^N states.
 * ``diagnostics``  the inverse-metric diagnostics of Eq. 4 and the infidelity.
+* ``vit``          the transformer wavefunction (embedding, encoder layers, output) whose
+                   modules give the block partition of Sec. 2.
 * ``vmc``          exchange-move Metropolis sampling of |psi|^2 and the VMC loop
                    (sample, block-layer SR step, theta += dtheta).
 
@@ -26,4 +28,4 @@ tests in ``tests/test_oracle_*.py`` except the Table 1 diagnostics values,
 which need the paper's trained network (parity unpinned for those numbers;
 the diagnostic formulas themselves are pinned by identities).
 """
-from . import nqs, hamiltonian, qgt, exact, diagnostics, vmc  # noqa: F401
+from . import nqs, hamiltonian, qgt, exact, diagnostics, vmc, vit  # noqa: F401

@@ -9,6 +9,7 @@ paragraph). Two architectures, with the flat parameter layouts of
 RBM:   ln psi(x) = sum_i a_i x_i + sum_j lncosh(b_j + sum_i W_ji x_i)
 FFNN:  h_0 = x; z_l = W_l h_{l-1} + b_l; h_l = lncosh(z_l) (hidden layers);
        ln psi = W_L h_{L-1} + b_L (one output)
+VIT:   the transformer of ``oracle.vit`` (both functions dispatch there)
 
 ln cosh branch (the paper is silent): lncosh(z) = s z - ln 2 + log1p(exp(-2 s z))
 with s = sign(Re z) (s = +1 at Re z = 0). It is holomorphic away from the
@@ -19,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from workloads import FFNN, RBM, Model
+from workloads import FFNN, RBM, VIT, Model
 
 LN2 = np.log(2.0)
 
@@ -56,6 +57,9 @@ def log_psi(model: Model, theta: np.ndarray, x: np.ndarray) -> np.ndarray:
     """ln psi for every row of x (int or float, values +-1). complex128 [n_s]."""
     x = np.asarray(x, dtype=np.float64)
     theta = np.asarray(theta, dtype=np.complex128)
+    if model.kind == VIT:
+        from . import vit
+        return vit.log_psi(model, theta, x)
     if model.kind == RBM:
         a, b, w = split_rbm(model, theta)
         th = x @ w.T + b
@@ -79,6 +83,9 @@ def jacobian(model: Model, theta: np.ndarray, x: np.ndarray):
     """
     x = np.asarray(x, dtype=np.float64)
     theta = np.asarray(theta, dtype=np.complex128)
+    if model.kind == VIT:
+        from . import vit
+        return vit.jacobian(model, theta, x)
     ns = x.shape[0]
     O = np.empty((ns, model.n_params), dtype=np.complex128)
     if model.kind == RBM:

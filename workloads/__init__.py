@@ -32,13 +32,20 @@ import numpy as np
 
 RBM = 0
 FFNN = 1
+VIT = 2
 
 
 @dataclasses.dataclass
 class Model:
     """A complex NQS architecture (no parameter values)."""
-    kind: int                      # RBM or FFNN
-    widths: Tuple[int, ...]        # FFNN: (N, h1, ..., 1); RBM: (N, M)
+    kind: int                      # RBM, FFNN or VIT
+    widths: Tuple[int, ...]        # FFNN: (N, h1, ..., 1); RBM: (N, M); VIT: (N, patch, d_model, d_mlp)
+    n_enc: int = 0                 # VIT: number of encoder layers
+
+    def vit_dims(self) -> Tuple[int, int, int, int, int]:
+        """(N, patch p, tokens T = N / p, d_model, d_mlp)."""
+        n, p, d, h = self.widths
+        return n, p, n // p, d, h
 
     @property
     def n_sites(self) -> int:
@@ -53,6 +60,11 @@ class Model:
         if self.kind == RBM:
             n, m = self.widths
             return [n, m, m * n]
+        if self.kind == VIT:
+            # embedding [W_E (d x p) | b_E]; per encoder layer [A (T x T) | W_V (d x d) |
+            # W_1 (h x d) | b_1 | W_2 (d x h) | b_2]; output [w_O (d) | b_O]
+            _, p, t, d, h = self.vit_dims()
+            return [d * p + d] + [t * t + d * d + 2 * h * d + h + d] * self.n_enc + [d + 1]
         return [o * i + o for (o, i) in self.layer_shapes()]
 
     def block_offsets(self) -> np.ndarray:
@@ -69,6 +81,16 @@ class Model:
         """Per-parameter std of each of the real and imaginary parts."""
         if self.kind == RBM:
             return np.full(self.n_params, 0.01)
+        if self.kind == VIT:
+            # fan-in law sqrt(1/(2 fan_in)) per part; the residual branches (attention A and
+            # the MLP's W_2, b_2) at half that, so that the encoder starts near the identity
+            _, p, t, d, h = self.vit_dims()
+            s = lambda fan, k: np.full(k, math.sqrt(1.0 / (2.0 * fan)))
+            parts = [s(p, d * p + d)]
+            for _ in range(self.n_enc):
+                parts += [0.5 * s(t, t * t), s(d, d * d), s(d, h * d + h), 0.5 * s(h, d * h + d)]
+            parts.append(s(d, d + 1))
+            return np.concatenate(parts)
         parts = []
         for (o, i) in self.layer_shapes():
             s = math.sqrt(1.0 / (2.0 * i))
@@ -167,6 +189,10 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
     * ``batch8x8_<i>``     instance i (0..15) of the batched 8x8 workload.
     * ``chain16_rbm``      RBM alpha=2 on the 16-site Heisenberg chain (the chain of Table 2),
       Marshall sign rule, 1024 samples, FP64: the starting point of the VMC training loop.
+    * ``chain16_vit``      the same chain with a two-encoder-layer transformer (4 tokens of 4
+      spins, d_model 16, MLP 32): blocks embedding / encoder 1 / encoder 2 / output.
+    * ``j1j2_6x6_vit``     6x6 J1-J2 with a transformer (9 tokens of 4 spins, d_model 32, MLP 64,
+      two encoder layers), 4096 samples, five-slice split.
     The last two also use the five-slice split: the two-slice (hi + lo) split misses the
     1e-6 dtheta bar by orders of magnitude on these lattices.
     """
@@ -214,6 +240,24 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
         # spectrum); without it the RBM loop stalls near 0.8 of the ground energy
         return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
                         1e-3, 1e-10, "fp64", 1.0, -1)
+    if name == "chain16_vit":
+        # the chain of Table 2 with a transformer: patches of 4 spins (4 tokens), d_model 16,
+        # MLP width 32, two encoder layers (the paper's "two-layer encoder")
+        model = Model(VIT, (16, 4, 16, 32), 2)
+        theta = init_params(model, np.random.default_rng(22))
+        ns = 1024 if n_samples is None else n_samples
+        configs = zero_sz_configs(16, ns, np.random.default_rng(23))
+        ij, jj = chain_bonds(16, 1.0)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "fp64", 1.0, -1)
+    if name == "j1j2_6x6_vit":
+        model = Model(VIT, (36, 4, 32, 64), 2)
+        theta = init_params(model, np.random.default_rng(24))
+        ns = 4096 if n_samples is None else n_samples
+        configs = zero_sz_configs(36, ns, np.random.default_rng(25))
+        ij, jj = square_j1j2_bonds(6, 6, 1.0, 0.5)
+        return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
+                        1e-3, 1e-10, "split_bf16_exact")
     if name.startswith("batch8x8_"):
         i = int(name.split("_")[1])
         if not 0 <= i < 16:
