@@ -102,7 +102,7 @@ typedef enum {
  * one-layer networks always take the NQS_FP64 arithmetic. */
 #define NQS_ELOC_DIFF32 8
 
-enum { NQS_RBM = 0, NQS_FFNN = 1 };
+enum { NQS_RBM = 0, NQS_FFNN = 1, NQS_VIT = 2 };
 
 /* Network description (host struct; host pointer `widths`).
  * RBM : widths = {N, M}; ln psi = sum_i a_i x_i + sum_j lncosh(b_j + sum_i W_ji x_i);
@@ -110,12 +110,26 @@ enum { NQS_RBM = 0, NQS_FFNN = 1 };
  * FFNN: widths = {N, h_1, ..., h_{L-1}, 1}; hidden layers z = W h + b, h' = lncosh(z),
  *       last layer linear; layout per layer [W_l (out x in row-major) | b_l]; one
  *       block per layer (Eq. 3: one block per module).
+ * VIT : the transformer whose modules define the block partition of Sec. 2 (patching and
+ *       embedding, encoder layers, output layer); the paper leaves the network unspecified,
+ *       this is a holomorphic variant (complex parameters, no layer norm, position-only
+ *       attention). widths = {N, p, d, h} (always four entries), n_layers = number of encoder
+ *       layers L >= 0; tokens T = N / p (p divides N), token t = spins t p .. t p + p - 1:
+ *         h_t = W_E x_t + b_E;
+ *         per encoder layer: u_t = h_t + sum_s A_ts W_V h_s,
+ *                            h_t <- u_t + W_2 lncosh(W_1 u_t + b_1) + b_2;
+ *         ln psi = w_O . sum_t lncosh(h_t) + b_O.
+ *       Layout: [W_E (d x p) | b_E (d)], then per encoder layer [A (T x T) | W_V (d x d) |
+ *       W_1 (h x d) | b_1 (h) | W_2 (d x h) | b_2 (d)], then [w_O (d) | b_O (1)]: L + 2 blocks.
+ *       FP64 only (NQS_FP64 and the split precisions, whose Jacobian and local energies are
+ *       FP64); NQS_FP32 is NQS_ERR_UNSUPPORTED. Limits: T <= 64, d <= 128, h <= 256,
+ *       T (3 d + h) <= 6144.
  * lncosh(z) = s z - ln 2 + log1p(exp(-2 s z)), s = sign(Re z) (s = +1 at Re z = 0).
  * Limits of this build: N <= 1024, every width <= 512, n_layers <= 32. */
 typedef struct {
-    int32_t kind;           /* NQS_RBM or NQS_FFNN */
-    int32_t n_layers;       /* number of weight layers (RBM: 1) = len(widths) - 1 */
-    const int32_t* widths;  /* HOST array of n_layers + 1 entries */
+    int32_t kind;           /* NQS_RBM, NQS_FFNN or NQS_VIT */
+    int32_t n_layers;       /* number of weight layers (RBM: 1) = len(widths) - 1; VIT: encoder layers */
+    const int32_t* widths;  /* HOST array of n_layers + 1 entries (VIT: 4) */
 } nqs_model;
 
 /* Spin Hamiltonian H = c * sum_b J_b (sx_i sx_j + sy_i sy_j + sz_i sz_j) over a bond

@@ -21,7 +21,7 @@ NQS_ERR_UNSUPPORTED = -7
 NQS_ERR_RETRY = -8
 
 NQS_FP64, NQS_FP32, NQS_SPLIT_BF16, NQS_SPLIT_BF16X3, NQS_SPLIT_BF16_EXACT = 0, 1, 2, 3, 4
-NQS_RBM, NQS_FFNN = 0, 1
+NQS_RBM, NQS_FFNN, NQS_VIT = 0, 1, 2
 NQS_SYNC = 1
 NQS_GRAPH = 2
 NQS_PARAM_SPACE = 4

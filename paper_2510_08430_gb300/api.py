@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_SPLIT_BF16_EXACT, NQS_SPLIT_BF16X3,
+from ._lib import (NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_VIT, NQS_SPLIT_BF16, NQS_SPLIT_BF16_EXACT, NQS_SPLIT_BF16X3,
                    NQS_ELOC_DIFF32, NQS_GRAPH, NQS_PARAM_SPACE, NQS_SYNC, check, nqs_hamiltonian, nqs_model)
 
 PRECISIONS = {"fp64": NQS_FP64, "fp32": NQS_FP32, "split_bf16": NQS_SPLIT_BF16, "split_bf16x3": NQS_SPLIT_BF16X3,
@@ -51,22 +51,29 @@ def _on(*tensors):
 
 
 class Model:
-    """Network description: kind (0 RBM, 1 FFNN) and widths."""
+    """Network description: kind (0 RBM, 1 FFNN, 2 VIT), widths, and for the transformer the
+    number of encoder layers (widths = (N, patch, d_model, d_mlp))."""
 
-    def __init__(self, kind: int, widths: Sequence[int]):
+    def __init__(self, kind: int, widths: Sequence[int], n_enc: int = 0):
         self.kind = int(kind)
         self.widths = [int(w) for w in widths]
+        self.n_enc = int(n_enc)
         self._w = (C.c_int32 * len(self.widths))(*self.widths)
-        self.c = nqs_model(self.kind, len(self.widths) - 1, self._w)
+        n_layers = self.n_enc if self.kind == NQS_VIT else len(self.widths) - 1
+        self.c = nqs_model(self.kind, n_layers, self._w)
 
     @classmethod
     def from_workload(cls, m) -> "Model":
-        return cls(m.kind, m.widths)
+        return cls(m.kind, m.widths, getattr(m, "n_enc", 0))
 
     def block_offsets(self) -> np.ndarray:
         if self.kind == NQS_RBM:
             n, m = self.widths
             sz = [n, m, m * n]
+        elif self.kind == NQS_VIT:
+            n, p, d, h = self.widths
+            t = n // p
+            sz = [d * p + d] + [t * t + d * d + 2 * h * d + h + d] * self.n_enc + [d + 1]
         else:
             sz = [self.widths[i + 1] * self.widths[i] + self.widths[i + 1] for i in range(len(self.widths) - 1)]
         return np.concatenate([[0], np.cumsum(sz)]).astype(np.int64)

@@ -460,7 +460,7 @@ int run_step_wide(const ModelDesc& md, const HamDesc& hd, const void* theta, con
     int rc = run_model(md, rp, theta, configs, ns, w.jb, st);
     if (rc) return rc;
     CK(launch_backward(rp, md, w.jb.thR, w.jb.Z, ns, w.jb.G, st), "backward");
-    CK(launch_jac_write(rp, md, w.jb.Z, w.jb.G, configs, ns, w.O, w.ldo, st), "jacobian");
+    CK(launch_jac_write(rp, md, w.jb.thR, w.jb.Z, w.jb.G, configs, ns, w.O, w.ldo, st), "jacobian");
     if (tm) CK(cudaEventRecord(ws->ev[1], st), "event");
     if (re != rp) {
         rc = run_model(md, re, theta, configs, ns, w.jbe, st);
@@ -706,6 +706,8 @@ int nqs_jacobian_workspace_size(const nqs_model* m, int64_t n_s, int32_t precisi
     ModelDesc md;
     if (!bytes || n_s < 1 || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     Arena a = sizing_arena();
     JacBufs jb;
     plan_model(a, md, n_s, jac_prec(precision), &jb, true);
@@ -718,6 +720,8 @@ int nqs_local_energy_workspace_size(const nqs_model* m, int64_t n_s, const nqs_h
     ModelDesc md;
     if (!bytes || n_s < 1 || !h || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     Arena a = sizing_arena();
     JacBufs jb;
     plan_model(a, md, n_s, eloc_prec(precision), &jb, false);
@@ -769,6 +773,8 @@ int sr_step_workspace_size(const nqs_model* m, int64_t n_s, const nqs_hamiltonia
     ModelDesc md;
     if (!bytes || n_s < 1 || !h || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     int rc = check_offsets(block_off, n_blocks, md.n_p);
     if (rc) return rc;
     Arena a = sizing_arena();
@@ -790,6 +796,8 @@ int sr_step_workspace_size2(const nqs_model* m, int64_t n_s, const nqs_hamiltoni
     ModelDesc md;
     if (!bytes || n_s < 1 || !h || check_prec(precision)) return fail(NQS_ERR_INVALID_ARG, "bad arguments");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     int rc = check_offsets(block_off, n_blocks, md.n_p);
     if (rc) return rc;
     WidePlan* wp = new (std::nothrow) WidePlan;
@@ -815,6 +823,8 @@ int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, i
     if (n_s < 1 || !theta || !configs || !logpsi_out || !O_out || ldo < n_s)
         return fail(NQS_ERR_INVALID_ARG, "nqs_jacobian: NULL pointer, n_s < 1 or ldo < n_s");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     Arena a = arena_of(ws);
     JacBufs jb;
     plan_model(a, md, n_s, jac_prec(precision), &jb, true);
@@ -825,7 +835,7 @@ int nqs_jacobian(const nqs_model* m, const void* theta, const int8_t* configs, i
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
     CK(launch_backward(rp, md, jb.thR, jb.Z, n_s, jb.G, st), "backward");
-    CK(launch_jac_write(rp, md, jb.Z, jb.G, configs, n_s, O_out, ldo, st), "jacobian");
+    CK(launch_jac_write(rp, md, jb.thR, jb.Z, jb.G, configs, n_s, O_out, ldo, st), "jacobian");
     CK(cudaMemcpyAsync(logpsi_out, jb.logpsi, sizeof(c128) * n_s, cudaMemcpyDeviceToDevice, st), "logpsi copy");
     return NQS_OK;
 }
@@ -855,6 +865,8 @@ int nqs_local_energy_ex(const nqs_model* m, const void* theta, const int8_t* con
         return fail(NQS_ERR_INVALID_ARG, "nqs_local_energy_ex: bad flags (NQS_ELOC_DIFF32 needs an FP64 forward)");
     if (n_s < 1 || !theta || !configs || !eloc_out) return fail(NQS_ERR_INVALID_ARG, "nqs_local_energy: bad arguments");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     int rc = ham_desc(h, md.N, &hd);
     if (rc) return rc;
     Arena a = arena_of(ws);
@@ -1125,6 +1137,8 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     if ((flags & NQS_ELOC_DIFF32) && precision == NQS_FP32)
         return fail(NQS_ERR_INVALID_ARG, "sr_step: NQS_ELOC_DIFF32 needs an FP64 forward (not NQS_FP32)");
     if (build_model_desc(m, n_s, &md)) return fail(NQS_ERR_INVALID_ARG, "bad model description");
+    if (md.kind == NQS_VIT && precision == NQS_FP32)
+        return fail(NQS_ERR_UNSUPPORTED, "the transformer runs in FP64 only (not NQS_FP32)");
     int rc = ham_desc(h, md.N, &hd);
     if (rc) return rc;
     rc = check_offsets(block_off, n_blocks, md.n_p);
@@ -1179,7 +1193,7 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     rc = run_model(md, rp, theta, configs, n_s, jb, st);
     if (rc) return rc;
     CK(launch_backward(rp, md, jb.thR, jb.Z, n_s, jb.G, st), "backward");
-    CK(launch_jac_write(rp, md, jb.Z, jb.G, configs, n_s, O, ldo, st), "jacobian");
+    CK(launch_jac_write(rp, md, jb.thR, jb.Z, jb.G, configs, n_s, O, ldo, st), "jacobian");
     if (tm) CK(cudaEventRecord(ws->ev[1], st), "event");
     if (re != rp) {
         rc = run_model(md, re, theta, configs, n_s, jbe, st);
@@ -1240,6 +1254,8 @@ int plan_batch(int n_inst, const nqs_model* models, const int64_t* n_s, const nq
         HamDesc hd;
         if (n_s[i] < 1) return fail(NQS_ERR_INVALID_ARG, "instance %d: n_s < 1", i);
         if (build_model_desc(&models[i], n_s[i], &md)) return fail(NQS_ERR_INVALID_ARG, "instance %d: bad model", i);
+        if (md.kind == NQS_VIT && prec == NQS_FP32)
+            return fail(NQS_ERR_UNSUPPORTED, "instance %d: the transformer runs in FP64 only", i);
         int rc = ham_desc(&hams[i], md.N, &hd);
         if (rc) return rc;
         rc = check_offsets(off, n_blocks[i], md.n_p);
@@ -1370,7 +1386,7 @@ extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const vo
         rc = run_model(md, rp, th, xc, ns, jb, st);
         if (!rc) {
             cudaError_t err = launch_backward(rp, md, jb.thR, jb.Z, ns, jb.G, st);
-            if (err == cudaSuccess) err = launch_jac_write(rp, md, jb.Z, jb.G, xc, ns, O, ldo, st);
+            if (err == cudaSuccess) err = launch_jac_write(rp, md, jb.thR, jb.Z, jb.G, xc, ns, O, ldo, st);
             if (err != cudaSuccess) rc = cuda_fail(err, "jacobian");
         }
         if (!rc && re != rp) rc = run_model(md, re, th, xc, ns, jbe, st);

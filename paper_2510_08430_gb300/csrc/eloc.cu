@@ -877,6 +877,10 @@ cudaError_t launch_conn_terms(int prec, const ModelDesc& md, const void* thR, co
                               const void* Z, const c128* logpsi, const int8_t* x, const HamDesc& h,
                               const int32_t* conn_bond, const int32_t* conn_sample,
                               const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st) {
+    if (md.kind == NQS_VIT)
+        return prec == NQS_FP64 ? launch_vit_conn_terms(md, (const c128*)thR, logpsi, x, h, conn_bond, conn_sample,
+                                                        nconn_ptr, max_conn, terms, st)
+                                : cudaErrorNotSupported;
     if (prec == NQS_FP64 && md.kind == NQS_FFNN && md.L >= 2 && wdf) {
         if (max_conn <= 0) return cudaSuccess;
         long long tr = 180000LL / (2LL * md.maxw * (long long)sizeof(c128));

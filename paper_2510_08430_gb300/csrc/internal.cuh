@@ -22,7 +22,13 @@ struct ModelDesc {
     long long wtoff[MAXL];      // W_l^T offset in the transposed-weight copy (in x out)
     long long zoff[MAXL];       // Z_l offset in the activation store ([n_s][out_l])
     long long aoff;             // RBM visible bias offset (0)
+    // transformer (NQS_VIT): patch p, tokens T = N / p, model width d, MLP width h, L encoder
+    // layers; vE parameters per encoder layer; vsave saved activations per sample
+    int vp, vT, vd, vh;
+    long long vE, vsave;
 };
+// transformer limits: T <= 64, d <= 128, h <= 256, T (3 d + h) <= VIT_SMEM_CX complex values
+constexpr int VIT_SMEM_CX = 6144;
 
 int build_model_desc(const nqs_model* m, long long ns, ModelDesc* md);  // returns status
 long long model_wt_elems(const ModelDesc& md);     // transposed weight copy size
@@ -39,7 +45,7 @@ cudaError_t launch_forward(int prec, const ModelDesc& md, const void* thR, const
 cudaError_t launch_backward(int prec, const ModelDesc& md, const void* thR, const void* Z,
                             long long ns, void* G, cudaStream_t st);
 // Jacobian (parameter-major) from Z, G and x
-cudaError_t launch_jac_write(int prec, const ModelDesc& md, const void* Z, const void* G,
+cudaError_t launch_jac_write(int prec, const ModelDesc& md, const void* thR, const void* Z, const void* G,
                              const int8_t* x, long long ns, void* O, long long ldo, cudaStream_t st);
 
 // ---- local energy ----
@@ -78,6 +84,16 @@ cudaError_t launch_conn_terms_dp(const ModelDesc& md, const void* thR, const voi
                                  const void* Z, const c128* logpsi, const int8_t* x, long long ns, const HamDesc& h,
                                  const int32_t* conn_bond, const int32_t* conn_sample, const long long* nconn_ptr,
                                  long long max_conn, c128* terms, const DpBufs& b, cudaStream_t st);
+// ---- transformer wavefunction (vit.cu): forward with saved activations (Z: [n_s][vsave]),
+// Jacobian rows (O[k * ldo + s], zero for n_s <= s < ldo), connected-configuration terms ----
+cudaError_t launch_vit_forward(const ModelDesc& md, const c128* th, const int8_t* x, long long ns, c128* Z,
+                               c128* logpsi, cudaStream_t st);
+cudaError_t launch_vit_jacobian(const ModelDesc& md, const c128* th, const c128* Z, const int8_t* x, long long ns,
+                                c128* O, long long ldo, cudaStream_t st);
+cudaError_t launch_vit_conn_terms(const ModelDesc& md, const c128* th, const c128* logpsi, const int8_t* x,
+                                  const HamDesc& h, const int32_t* conn_bond, const int32_t* conn_sample,
+                                  const long long* nconn_ptr, long long max_conn, c128* terms, cudaStream_t st);
+
 // ---- exchange-move Metropolis sampler and parameter update (sampler.cu) ----
 cudaError_t launch_mc_setup(long long n, double* bond_J, int32_t* csamp, int32_t* cbond, long long* nconn,
                             cudaStream_t st);

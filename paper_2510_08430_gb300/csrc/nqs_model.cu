@@ -8,7 +8,35 @@
 
 namespace nqs {
 
+static int build_vit_desc(const nqs_model* m, long long ns, ModelDesc* md) {
+    const int N = m->widths[0], p = m->widths[1], d = m->widths[2], h = m->widths[3], L = m->n_layers;
+    if (N < 2 || N > MAXN || p < 1 || N % p || d < 1 || d > 128 || h < 1 || h > 256 || L < 0 || L > MAXL)
+        return NQS_ERR_INVALID_ARG;
+    const int T = N / p;
+    if (T > 64 || (long long)T * (3 * d + h) > VIT_SMEM_CX) return NQS_ERR_INVALID_ARG;
+    md->kind = NQS_VIT;
+    md->L = L;
+    md->N = N;
+    for (int i = 0; i < 4; ++i) md->widths[i] = m->widths[i];
+    md->maxw = d > h ? d : h;
+    md->vp = p;
+    md->vT = T;
+    md->vd = d;
+    md->vh = h;
+    md->vE = (long long)T * T + (long long)d * d + 2LL * h * d + h + d;
+    md->vsave = (long long)T * d + (long long)L * (3LL * T * d + (long long)T * h);
+    const long long np = (long long)d * p + d + L * md->vE + d + 1;
+    if (np > 0x7fffffffLL) return NQS_ERR_INVALID_ARG;
+    md->n_p = (int)np;
+    (void)ns;
+    return NQS_OK;
+}
+
 int build_model_desc(const nqs_model* m, long long ns, ModelDesc* md) {
+    if (m && m->kind == NQS_VIT && m->widths) {
+        *md = ModelDesc{};
+        return build_vit_desc(m, ns, md);
+    }
     if (!m || !m->widths || m->n_layers < 1 || m->n_layers > MAXL) return NQS_ERR_INVALID_ARG;
     *md = ModelDesc{};
     md->kind = m->kind;
@@ -52,11 +80,13 @@ int build_model_desc(const nqs_model* m, long long ns, ModelDesc* md) {
 }
 
 long long model_wt_elems(const ModelDesc& md) {
+    if (md.kind == NQS_VIT) return 0;
     long long t = 0;
     for (int l = 0; l < md.L; ++l) t += (long long)md.widths[l + 1] * md.widths[l];
     return t;
 }
 long long model_z_elems(const ModelDesc& md, long long ns) {
+    if (md.kind == NQS_VIT) return ns * md.vsave;
     long long t = 0;
     for (int l = 0; l < md.L; ++l) t += ns * md.widths[l + 1];
     return t;
@@ -71,7 +101,7 @@ __global__ void prepare_params_kernel(ModelDesc md, const c128* __restrict__ th,
          p += (long long)gridDim.x * blockDim.x) {
         const cx<R> v = ccast<R>(th[p]);
         thR[p] = v;
-        for (int l = 0; l < md.L; ++l) {
+        for (int l = 0; l < (md.kind == NQS_VIT ? 0 : md.L); ++l) {
             const long long o = md.widths[l + 1], in = md.widths[l];
             if (p >= md.woff[l] && p < md.woff[l] + o * in) {
                 const long long q = p - md.woff[l];
@@ -347,16 +377,23 @@ cudaError_t launch_prepare_params(int prec, const ModelDesc& md, const void* the
 }
 cudaError_t launch_forward(int prec, const ModelDesc& md, const void* thR, const void* wtR,
                            const int8_t* x, long long ns, void* Z, c128* logpsi, cudaStream_t st) {
+    if (md.kind == NQS_VIT)
+        return prec == NQS_FP64 ? launch_vit_forward(md, (const c128*)thR, x, ns, (c128*)Z, logpsi, st)
+                                : cudaErrorNotSupported;
     return prec == NQS_FP64 ? forward_t<double>(md, thR, wtR, x, ns, Z, logpsi, st)
                             : forward_t<float>(md, thR, wtR, x, ns, Z, logpsi, st);
 }
 cudaError_t launch_backward(int prec, const ModelDesc& md, const void* thR, const void* Z,
                             long long ns, void* G, cudaStream_t st) {
+    if (md.kind == NQS_VIT) return cudaSuccess;  // the transformer's backward runs in launch_jac_write
     return prec == NQS_FP64 ? backward_t<double>(md, thR, Z, ns, G, st)
                             : backward_t<float>(md, thR, Z, ns, G, st);
 }
-cudaError_t launch_jac_write(int prec, const ModelDesc& md, const void* Z, const void* G,
+cudaError_t launch_jac_write(int prec, const ModelDesc& md, const void* thR, const void* Z, const void* G,
                              const int8_t* x, long long ns, void* O, long long ldo, cudaStream_t st) {
+    if (md.kind == NQS_VIT)
+        return prec == NQS_FP64 ? launch_vit_jacobian(md, (const c128*)thR, (const c128*)Z, x, ns, (c128*)O, ldo, st)
+                                : cudaErrorNotSupported;
     return prec == NQS_FP64 ? jac_t<double>(md, Z, G, x, ns, O, ldo, st)
                             : jac_t<float>(md, Z, G, x, ns, O, ldo, st);
 }

@@ -115,6 +115,13 @@ def test_newer_entry_points_validate_on_the_host(lib):
     assert lib.nqs_theta_update(None, fake, 4, None) == -1
     out = C.c_size_t(0)
     assert lib.nqs_metropolis_workspace_size(C.byref(m.c), 64, C.byref(out)) == 0 and out.value > 0
+    # transformer: FP64 only; the patch must divide N
+    import paper_2510_08430_gb300 as nq
+    vit = nq.Model(2, [16, 4, 16, 32], 2)
+    assert lib.nqs_jacobian_workspace_size(C.byref(vit.c), 64, 0, C.byref(out)) == 0
+    assert lib.nqs_jacobian_workspace_size(C.byref(vit.c), 64, 1, C.byref(out)) == -7
+    bad = nq.Model(2, [16, 5, 16, 32], 2)
+    assert lib.nqs_jacobian_workspace_size(C.byref(bad.c), 64, 0, C.byref(out)) == -1
     # shard sums and VJP: leading dimension below n_s
     assert lib.nqs_shard_sums(fake, 10, 64, 10, 0, fake, fake, fake, None) == -1
     assert lib.nqs_vjp(fake, 10, 64, 10, 0, fake, fake, None) == -1

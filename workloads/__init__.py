@@ -82,10 +82,11 @@ class Model:
         if self.kind == RBM:
             return np.full(self.n_params, 0.01)
         if self.kind == VIT:
-            # fan-in law sqrt(1/(2 fan_in)) per part; the residual branches (attention A and
-            # the MLP's W_2, b_2) at half that, so that the encoder starts near the identity
+            # a tenth of the fan-in law sqrt(1/(2 fan_in)) per part (a nearly uniform start, as
+            # the RBM's 0.01); the residual branches (attention A and the MLP's W_2, b_2) at
+            # half that, so that the encoder starts near the identity
             _, p, t, d, h = self.vit_dims()
-            s = lambda fan, k: np.full(k, math.sqrt(1.0 / (2.0 * fan)))
+            s = lambda fan, k: np.full(k, 0.1 * math.sqrt(1.0 / (2.0 * fan)))
             parts = [s(p, d * p + d)]
             for _ in range(self.n_enc):
                 parts += [0.5 * s(t, t * t), s(d, d * d), s(d, h * d + h), 0.5 * s(h, d * h + d)]
@@ -248,8 +249,9 @@ def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
         ns = 1024 if n_samples is None else n_samples
         configs = zero_sz_configs(16, ns, np.random.default_rng(23))
         ij, jj = chain_bonds(16, 1.0)
+        # shift 1e-2: with 1e-3 the first SR steps of the nearly uniform start are too long
         return Workload(name, model, theta, configs, ij, jj, model.block_offsets(),
-                        1e-3, 1e-10, "fp64", 1.0, -1)
+                        1e-2, 1e-10, "fp64", 1.0, -1)
     if name == "j1j2_6x6_vit":
         model = Model(VIT, (36, 4, 32, 64), 2)
         theta = init_params(model, np.random.default_rng(24))
