@@ -350,24 +350,26 @@ def compare_steps(nq, torch, np, w, model, ham, theta, x, dth, solver) -> dict:
 VMC_ITERS, VMC_STEPS = 40, 16
 
 
-def vmc_gpu(nq, torch, np) -> dict:
-    """The device VMC loop (NEXT #3) on the 16-site chain of Table 2: RBM alpha = 2, 1024
-    chains, 16 exchange-move Metropolis steps and one block-layer SR step per iteration. Its
-    energy is set against Table 2's block-layer value (Pauli units)."""
+def vmc_gpu(nq, torch, np, name="chain16_rbm", eta=0.05, full_qgt=False) -> dict:
+    """The device VMC loop (NEXT #3) on the 16-site chain of Table 2: 1024 chains, 16
+    exchange-move Metropolis steps and one SR step per iteration, from the random start. The
+    energy is set against Table 2's block-layer value (Pauli units). For the transformer
+    (NEXT #4) the module partition (embedding / encoder layers / output) or the full QGT."""
     import workloads as W
-    w = W.make_workload("chain16_rbm")
+    w = W.make_workload(name)
     model = nq.Model.from_workload(w.model)
     theta = torch.as_tensor(w.theta, device="cuda")
     x = torch.as_tensor(w.configs, device="cuda")
     ham = nq.Hamiltonian(w.model.n_sites, w.bond_ij, w.bond_j, w.c, w.sign_rule)
+    off = np.array([0, w.model.n_params], dtype=np.int64) if full_qgt else w.block_off
     g = torch.Generator(device="cuda").manual_seed(7)
-    nq.vmc_train(model, theta.clone(), x.clone(), ham, w.block_off, 2, VMC_STEPS, w.diag_shift, w.cutoff, 0.05,
+    nq.vmc_train(model, theta.clone(), x.clone(), ham, off, 2, VMC_STEPS, w.diag_shift, w.cutoff, eta,
                  "fp64", "mixed", generator=g)  # warm-up
     torch.cuda.synchronize()
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     s.record()
-    out = nq.vmc_train(model, theta, x, ham, w.block_off, VMC_ITERS, VMC_STEPS, w.diag_shift, w.cutoff, 0.05,
+    out = nq.vmc_train(model, theta, x, ham, off, VMC_ITERS, VMC_STEPS, w.diag_shift, w.cutoff, eta,
                        "fp64", "mixed", generator=g)
     e.record()
     e.synchronize()
@@ -375,8 +377,9 @@ def vmc_gpu(nq, torch, np) -> dict:
     e_last = float(np.mean(out["energies"][-10:].real))
     with open(os.path.join(ROOT, "tests", "golden", "paper_values.json")) as f:
         ref = float(json.load(f)["table2_block_energy"]["value"])
-    return {"workload": f"chain16_rbm: RBM (16, 32), 1024 chains, {VMC_STEPS} Metropolis steps + 1 SR step "
-                        f"per iteration, {VMC_ITERS} iterations from the random start",
+    return {"workload": f"{name}: n_p {w.model.n_params}, blocks {[int(v) for v in np.diff(off)]}, 1024 chains, "
+                        f"{VMC_STEPS} Metropolis steps + 1 SR step per iteration, {VMC_ITERS} iterations "
+                        f"from the random start, eta {eta}, shift {w.diag_shift}",
             "seconds_per_iteration": secs / VMC_ITERS, "iterations_per_s": VMC_ITERS / secs,
             "energy_last10": e_last, "table2_block_energy": ref,
             "rel_diff_vs_table2": (e_last - ref) / abs(ref),
@@ -600,10 +603,13 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         line["graph_replay"] = {"unavailable": str(exc)[:200]}
     if world == 1 and not args.no_fp64_compare:
         line["comparisons"] = compare_steps(nq, torch, np, w, model, ham, theta, x, dth_split, args.solver)
-        try:
-            line["comparisons"]["vmc_chain16"] = vmc_gpu(nq, torch, np)
-        except Exception as exc:
-            line["comparisons"]["vmc_chain16"] = {"unavailable": str(exc)[:200]}
+        for key, kw in (("vmc_chain16_rbm", {}),
+                        ("vmc_chain16_vit_block_qgt", {"name": "chain16_vit", "eta": 0.02}),
+                        ("vmc_chain16_vit_full_qgt", {"name": "chain16_vit", "eta": 0.02, "full_qgt": True})):
+            try:
+                line["comparisons"][key] = vmc_gpu(nq, torch, np, **kw)
+            except Exception as exc:
+                line["comparisons"][key] = {"unavailable": str(exc)[:200]}
     if world == 1 and not args.no_cpu_baseline:
         info = oracle_sample(w)
         one = oracle_sample_single_thread(w)
