@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--eloc", default="diff32", choices=["diff32", "fp64"],
                     help="local energies: FP32 difference propagation (NQS_ELOC_DIFF32; its dtheta is checked "
                          "against the FP64 oracle in the same run) or the FP64-class arithmetic")
+    ap.add_argument("--batch8x8", action="store_true",
+                    help="the 16-instance batched 8x8 workload (12-layer FFNNs, N_s 2048-8192) through "
+                         "sr_step_batched in instance groups that fit the memory budget")
+    ap.add_argument("--batch-budget-gb", type=float, default=150.0)
     ap.add_argument("--sharded", action="store_true",
                     help="split ONE instance over the ranks by samples (three exchanges over NCCL; strong scaling)")
     return ap.parse_args()
@@ -707,6 +711,69 @@ def run_sharded(args, rank: int, world: int, local_rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_batch8x8(args) -> None:
+    """All 16 instances of the batched 8x8 workload per step (one SR step of each), grouped by
+    plan_batch_chunks so that one reused workspace of at most --batch-budget-gb fits."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_08430_gb300 as nq
+    import workloads as W
+
+    ws_ = [W.make_workload(f"batch8x8_{i}") for i in range(16)]
+    models = [nq.Model.from_workload(w.model) for w in ws_]
+    hams = [nq.Hamiltonian(64, w.bond_ij, w.bond_j, w.c, w.sign_rule) for w in ws_]
+    thetas = [torch.as_tensor(w.theta, device="cuda") for w in ws_]
+    xs = [torch.as_tensor(w.configs, device="cuda") for w in ws_]
+    offs = [w.block_off for w in ws_]
+    ns = [w.n_samples for w in ws_]
+    groups, worst = nq.plan_batch_chunks(models, ns, hams, offs, int(args.batch_budget_gb * 1e9))
+    ws = nq.Workspace(worst)
+    shift, cutoff = ws_[0].diag_shift, ws_[0].cutoff
+
+    def step():
+        out = []
+        for g in groups:
+            d, em, _, _ = nq.sr_step_batched([models[i] for i in g], [thetas[i] for i in g], [xs[i] for i in g],
+                                             [hams[i] for i in g], [offs[i] for i in g], shift, cutoff, 1.0,
+                                             "split_bf16_exact", solver="mixed", ws=ws)
+            out += d
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        dths = step()
+    e.record()
+    e.synchronize()
+    secs = s.elapsed_time(e) / 1e3
+    # instance 0 against its own sr_step (parameter space, same precision and solver)
+    d0, _, _, _ = nq.sr_step(models[0], thetas[0], xs[0], hams[0], offs[0], shift, cutoff, 1.0, "split_bf16_exact",
+                             solver="mixed", want_evals=False, param_space=True)
+    diff0 = float(torch.linalg.norm(dths[0] - d0) / torch.linalg.norm(d0))
+    sq = sum(float(np.sum(np.diff(o).astype(np.float64) ** 2)) for o in offs)
+    gram_flops = sum(float(np.sum(4 * np.diff(o) * (np.diff(o) + 1.0))) * n for o, n in zip(offs, ns))
+    line = {"metric": "block-SR steps/s of the 16-instance batch", "value": args.steps / secs, "unit": "batch steps/s",
+            "instances_per_s": 16 * args.steps / secs, "ms_per_batch_step": 1e3 * secs / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 five-slice split Gram + f32 Cholesky + f64",
+            "data": "synthetic",
+            "config": {"workload": "batch8x8_0..15: FFNN 64-(32/64/128 cycling x 11)-1, 8x8 J1-J2 (J2 = 0.6 i/15), "
+                                   f"N_s {ns[0]}..{ns[-1]} (sum {sum(ns)}), blocks 65..8320, n_p 47937 each",
+                       "memory_plan": {"groups": groups, "workspace_gb": worst / 1e9,
+                                       "budget_gb": args.batch_budget_gb,
+                                       "all_at_once_gb": nq.sr_step_batched_workspace_size(models, ns, hams, offs) / 1e9},
+                       "sum_nb2": sq},
+            "gram_algorithmic_flops_per_batch_step": gram_flops,
+            "instance0_dtheta_rel_diff_vs_single_sr_step": diff0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -720,7 +787,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.sharded:
+    if args.batch8x8:
+        run_batch8x8(args)
+    elif args.sharded:
         run_sharded(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)

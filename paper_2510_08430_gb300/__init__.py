@@ -6,5 +6,6 @@ include/nqs_sr.h); this package is its thin Python binding.
 from .api import (Hamiltonian, Model, NQSLogPsi, SRStep, Workspace, born_weights, inverse_metric_study,  # noqa: F401
                   launch_count, log_psi, nqs_connections, nqs_jacobian, nqs_local_energy, ntk_solve, qgt_block_build,
                   qgt_block_build_static, qgt_block_solve, qgt_inverse_diagnostics, set_eloc_fallback_all, set_limits,
-                  sr_step, sr_step_batched, theta_update, metropolis, version, vmc_train)
+                  plan_batch_chunks, sr_step, sr_step_batched, sr_step_batched_workspace_size, theta_update,
+                  metropolis, version, vmc_train)
 from ._lib import NQS_FFNN, NQS_FP32, NQS_FP64, NQS_RBM, NQS_SPLIT_BF16, NQS_VIT, NQSError  # noqa: F401

@@ -379,25 +379,69 @@ def sr_step(model: Model, theta: torch.Tensor, configs: torch.Tensor, ham: Hamil
     return st.dtheta, st.emean, st.evals, st.n_kept
 
 
-def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float, cutoff: float, eta: float = 1.0,
-                    precision="split_bf16", cutoff_mode: int = 0, solver="mixed", want_evals: bool = False,
-                    eloc_diff32: bool = False):
-    """Several independent SR steps in one call (one grouped Gram and one eigensolver launch).
-    Lists of per-instance Model, theta (c128 device), configs (int8 device), Hamiltonian and block
-    offsets. Returns (list of dtheta, Emean c128 [n_inst], evals or None, n_kept int32 [sum blocks])."""
-    lib = _lib.load()
+def _batch_args(models, n_s, hams, block_offs):
     n = len(models)
     mods = (nqs_model * n)(*[m.c for m in models])
     hs = (nqs_hamiltonian * n)(*[h.c for h in hams])
-    ns = (C.c_int64 * n)(*[int(x.shape[0]) for x in configs])
+    ns = (C.c_int64 * n)(*[int(v) for v in n_s])
     nbs = (C.c_int32 * n)(*[len(o) - 1 for o in block_offs])
     offs = np.concatenate([np.asarray(o, dtype=np.int64) for o in block_offs])
     off_c = (C.c_int64 * len(offs))(*offs.tolist())
+    return n, mods, hs, ns, nbs, off_c
+
+
+def sr_step_batched_workspace_size(models, n_s, hams, block_offs, precision="split_bf16_exact") -> int:
+    """Bytes of workspace one sr_step_batched call over these instances needs."""
+    n, mods, hs, ns, nbs, off_c = _batch_args(models, n_s, hams, block_offs)
+    sz = C.c_size_t(0)
+    check(_lib.load().sr_step_batched_workspace_size(n, mods, ns, hs, off_c, nbs, _prec(precision), C.byref(sz)))
+    return int(sz.value)
+
+
+def plan_batch_chunks(models, n_s, hams, block_offs, max_bytes: int, precision="split_bf16_exact"):
+    """Memory plan of a batch that does not fit at once: consecutive groups of instances, each
+    as large as possible with its sr_step_batched workspace within max_bytes. Returns (list of
+    index lists, the largest group's workspace bytes); a single instance above max_bytes is an
+    error."""
+    groups, cur, worst = [], [], 0
+    for i in range(len(models)):
+        trial = cur + [i]
+        need = sr_step_batched_workspace_size([models[k] for k in trial], [n_s[k] for k in trial],
+                                              [hams[k] for k in trial], [block_offs[k] for k in trial], precision)
+        if need <= max_bytes:
+            cur, last = trial, need
+            continue
+        if not cur:
+            raise ValueError(f"instance {i} alone needs {need} bytes > {max_bytes}")
+        groups.append(cur)
+        worst = max(worst, last)
+        cur = [i]
+        last = sr_step_batched_workspace_size([models[i]], [n_s[i]], [hams[i]], [block_offs[i]], precision)
+        if last > max_bytes:
+            raise ValueError(f"instance {i} alone needs {last} bytes > {max_bytes}")
+    if cur:
+        groups.append(cur)
+        worst = max(worst, last)
+    return groups, worst
+
+
+def sr_step_batched(models, thetas, configs, hams, block_offs, diag_shift: float, cutoff: float, eta: float = 1.0,
+                    precision="split_bf16", cutoff_mode: int = 0, solver="mixed", want_evals: bool = False,
+                    eloc_diff32: bool = False, ws: Optional[Workspace] = None):
+    """Several independent SR steps in one call (one grouped Gram and one eigensolver launch).
+    Lists of per-instance Model, theta (c128 device), configs (int8 device), Hamiltonian and block
+    offsets. Returns (list of dtheta, Emean c128 [n_inst], evals or None, n_kept int32 [sum blocks]).
+    ws: a workspace to (grow and) reuse across calls."""
+    lib = _lib.load()
+    n, mods, hs, ns, nbs, off_c = _batch_args(models, [int(x.shape[0]) for x in configs], hams, block_offs)
     p = _prec(precision)
     sz = C.c_size_t(0)
     check(lib.sr_step_batched_workspace_size(n, mods, ns, hs, off_c, nbs, p, C.byref(sz)))
     dev = thetas[0].device
-    ws = Workspace(int(sz.value), device=dev)
+    if ws is None:
+        ws = Workspace(int(sz.value), device=dev)
+    else:
+        ws.ensure(int(sz.value))
     th = torch.cat([t.reshape(-1) for t in thetas]).contiguous()
     xc = torch.cat([x.reshape(-1) for x in configs]).contiguous()
     np_tot = int(th.numel())
