@@ -274,6 +274,30 @@ __device__ __forceinline__ void digits5(long long N, int (&d)[5]) {
     }
     d[0] = (int)N;
 }
+// round(x 2^k) to the nearest integer, ties to even, from the bits of x with integer
+// operations only (GB300's FP64 rate is a small fraction of its integer rate); exact for
+// |x 2^k| < 2^62. Equals __double2ll_rn(x * 2^k) wherever x * 2^k is exact.
+__device__ __forceinline__ long long scaled_round(double x, int k) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;  // zero or subnormal: far below one unit for every k used here
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);  // x = m 2^(e - 1075)
+    const int sh = 1075 - e - k;                                 // x 2^k = m 2^-sh
+    long long q;
+    if (sh <= 0) {
+        q = m << (-sh);
+    } else if (sh > 54) {
+        q = 0;
+    } else {
+        const long long rem = m & ((1LL << sh) - 1), half = 1LL << (sh - 1);
+        q = m >> sh;
+        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
+    }
+    return b < 0 ? -q : q;
+}
+// |x| as an integer: for non-negative doubles the bit patterns order like the values
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+
 constexpr int GROUP = GRAM_GROUP;  // samples per exponent group: one warp, one sample per lane
 static_assert(GROUP == 32, "one warp per exponent group");
 // The five slices (integers of at most 8 bits scaled by 2^-7, 2^-15, ..., 2^-39) of column c
@@ -309,6 +333,7 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
     const double u = 1.0 / (double)ns;
     const double uw = sa.wconst > 0.0 ? sa.wconst : u;  // weight of every sample when w is NULL
     double mr = 0.0, mi = 0.0;
+#pragma unroll 4
     for (long long s = threadIdx.x; s < (sa.mean_in ? 0 : ns); s += blockDim.x) {
         const c128 v = row[s];
         const double ws = w ? w[s] : 1.0;
@@ -325,43 +350,57 @@ __global__ void __launch_bounds__(256) center_group_kernel(const c128* __restric
         mr = sa.mean_in[p].re;
         mi = sa.mean_in[p].im;
     }
+    // with uniform weights the sums run unweighted and are scaled once at the end (fewer
+    // FP64 operations per element)
     double fr = 0.0, fi = 0.0, dg = 0.0;
     const int lane = threadIdx.x & 31;
     // blockDim.x is a multiple of 32 and ldk of GROUP: the samples of a group are one warp
+    // (the trip count is warp-uniform)
     for (long long s = threadIdx.x; s < ldk; s += blockDim.x) {
         double dr = 0.0, di = 0.0;
         if (s < ns) {
             const c128 v = row[s];
-            const double ws = w ? w[s] : uw;
             dr = v.re - mr;
             di = v.im - mi;
             const c128 es = e[s];
-            fr = fma(ws, fma(dr, es.re, di * es.im), fr);
-            fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
-            dg = fma(ws, fma(dr, dr, di * di), dg);
             if (w) {
+                const double ws = w[s];
+                fr = fma(ws, fma(dr, es.re, di * es.im), fr);
+                fi = fma(ws, fma(dr, es.im, -di * es.re), fi);
+                dg = fma(ws, fma(dr, dr, di * di), dg);
                 const double sw = sqrt(ws);
                 dr *= sw;
                 di *= sw;
+            } else {
+                fr = fma(dr, es.re, fma(di, es.im, fr));
+                fi = fma(dr, es.im, fma(-di, es.re, fi));
+                dg = fma(dr, dr, fma(di, di, dg));
             }
         }
-        double mx = fmax(fabs(dr), fabs(di));
+        long long mx = abs_bits(dr) > abs_bits(di) ? abs_bits(dr) : abs_bits(di);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = y > mx ? y : mx;
+        }
         // E with mx = m 2^E, m in [0.5, 1) (frexp convention), from the exponent bits
-        int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
-        ex = mx > 0.0 ? ex : 0;
+        int ex = (int)((mx >> 52) & 0x7ff) - 1022;
+        ex = mx != 0 ? ex : 0;
         ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
         if (lane == 0) gexp[(s / GROUP) * gstride + p] = (int8_t)ex;
-        const double sc = __longlong_as_double((long long)(1023 + 39 - ex) << 52);  // 2^(39 - E)
         int dr5[5], di5[5];
-        digits5(__double2ll_rn(dr * sc), dr5);
-        digits5(__double2ll_rn(di * sc), di5);
+        digits5(scaled_round(dr, 39 - ex), dr5);  // round(dr 2^(39 - E))
+        digits5(scaled_round(di, 39 - ex), di5);
         store_slices(p12, p34, p5, 2 * p, s, ldk, dr5, di5);
     }
     fr = block_sum(fr, sh);
     fi = block_sum(fi, sh);
     dg = block_sum(dg, sh);
+    if (!w) {
+        fr *= uw;
+        fi *= uw;
+        dg *= uw;
+    }
     if (threadIdx.x == 0) {
         F[p] = mk<double>(fr, fi);
         if (Omean) Omean[p] = mk<double>(mr, mi);
@@ -413,10 +452,9 @@ __global__ void __launch_bounds__(256) transpose_group_kernel(const c128* __rest
             gexp[(k0 / GROUP) * ns + s] = (int8_t)ex;
             if (d2 != 0.0) atomicAdd(diag + s, d2 * inv_ns);
         }
-        const double sc = __longlong_as_double((long long)(1023 + 39 - ex) << 52);  // 2^(39 - E)
         int dr5[5], di5[5];
-        digits5(__double2ll_rn(dr * sc), dr5);
-        digits5(__double2ll_rn(di * sc), di5);
+        digits5(scaled_round(dr, 39 - ex), dr5);  // round(dr 2^(39 - E))
+        digits5(scaled_round(di, 39 - ex), di5);
         const long long k = k0 + lane;
         if (k < ldk) store_slices(p12, p34, p5, 2 * s, k, ldk, dr5, di5);
     }

@@ -105,17 +105,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// try_wait that may suspend the thread in hardware for up to `ns` nanoseconds while the
+// phase is incomplete (a waiting warp then takes no issue slots from the working ones)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: false on timeout or (if abort_flag is not NULL) when another
-// role has aborted. The iteration cap backs up the time budget.
+// role has aborted. Each try suspends for at most 20 us; the iteration cap backs up the
+// time budget.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t it = 0; it < (1u << 30); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u) {
-            if (abort_flag && *abort_flag) return false;
-            if (gtimer() - t0 > WAIT_NS) return false;
-        }
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) return false;
     }
     return false;
 }

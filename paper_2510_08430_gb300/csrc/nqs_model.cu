@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(256) bwd_kernel(ModelDesc md, const cx<R>* __r
 // One CTA: 32 samples (one per lane) x JC output units x KC inputs; every warp
 // store writes 32 consecutive samples of one parameter row.
 constexpr int JAC_TS = 32;
-constexpr int JAC_JC = 16;
-constexpr int JAC_KC = 128;
+constexpr int JAC_JC = 64;  // output units per CTA: every h_{l-1} value is computed once per tile
+constexpr int JAC_KC = 32;
 template <typename R>
 __global__ void __launch_bounds__(256) jac_kernel(ModelDesc md, int l, const cx<R>* __restrict__ Z,
                                                    const cx<R>* __restrict__ G,
@@ -292,11 +292,21 @@ __global__ void __launch_bounds__(256) jac_kernel(ModelDesc md, int l, const cx<
     if (s >= ldo) return;
     const bool live = s < ns;
     const cx<R> zero = mk<R>(R(0), R(0));
-    const int npairs = jn * kn;
-    for (int p = wid; p < npairs; p += nw) {
-        const int jj = p / kn, kk = p % kn;
-        const long long row = md.woff[l] + (long long)(j0 + jj) * in + k0 + kk;
-        O[row * ldo + s] = live ? GT[jj][lane] * HT[kk][lane] : zero;
+    // warp w writes rows (j0 + jj, k0 .. k0 + kn) for jj = w, w + nw, ...: 32 samples (one
+    // 512-byte segment for c128) per store, four independent stores in flight per step
+    for (int jj = wid; jj < jn; jj += nw) {
+        const cx<R> g = live ? GT[jj][lane] : zero;
+        cx<R>* orow = O + (md.woff[l] + (long long)(j0 + jj) * in + k0) * ldo + s;
+        int kk = 0;
+        for (; kk + 4 <= kn; kk += 4) {
+            const cx<R> v0 = g * HT[kk][lane], v1 = g * HT[kk + 1][lane];
+            const cx<R> v2 = g * HT[kk + 2][lane], v3 = g * HT[kk + 3][lane];
+            orow[(long long)kk * ldo] = v0;
+            orow[(long long)(kk + 1) * ldo] = v1;
+            orow[(long long)(kk + 2) * ldo] = v2;
+            orow[(long long)(kk + 3) * ldo] = v3;
+        }
+        for (; kk < kn; ++kk) orow[(long long)kk * ldo] = g * HT[kk][lane];
     }
     if (blockIdx.z == 0) {
         for (int jj = wid; jj < jn; jj += nw)
