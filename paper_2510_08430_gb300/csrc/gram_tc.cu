@@ -70,6 +70,38 @@ template <> struct Split<5> {
     }
 };
 
+// Packed pairs of FP32 numbers (here: the real and imaginary part of one output), operated on
+// by the two-lane FP32 instructions of sm_100-class GPUs with round-to-nearest in each lane.
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// (s, e) with s + e = a + b exactly, lane by lane (TwoSum, Knuth)
+__device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e) {
+    s = add2(a, b);
+    const uint64_t bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
 // Error-free sum of two FP32 numbers: s + e = a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
@@ -441,9 +473,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const long long k = (long long)ti.I * (BM / 2) + (r >> 1);
             // double-float running sums of the 16 complex outputs this lane owns, renormalised
             // after every work item
-            float hre[16], lre[16], him[16], lim[16];
+            // (Re, Im) packed: high words hw[j], low words lw[j]
+            uint64_t hw[16], lw[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) hre[j] = lre[j] = him[j] = lim[j] = 0.f;
+            for (int j = 0; j < 16; ++j) hw[j] = lw[j] = 0ull;
             for (int item = 0; item < nitems; ++item, ++q) {
                 const uint32_t acc = q & 1u;
                 if (!mbar_wait(&tfull_bar[acc], (q >> 1) & 1u, abort_flag)) {
@@ -504,25 +537,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             }
                         }
                         const int j = 2 * chunk + m;
+                        uint64_t v0 = pk2(re0, im0), v1 = pk2(re1, im1);
                         if (GROUPED) {
                             const long long lcol = (long long)ti.J * (BM / 2) + 32 * half + 2 * j + cpar;
                             const int el = (lcol < n) ? (int)gcol[2 * j + cpar] : 0;
                             const int es = ekg + el;  // 2^(E_k + E_l), exact
                             const float f = (es >= -126 && es <= 127) ? __int_as_float((es + 127) << 23)
                                                                       : ldexpf(1.f, es);
-                            re0 *= f;
-                            im0 *= f;
-                            re1 *= f;
-                            im1 *= f;
+                            const uint64_t ff = pk2(f, f);
+                            v0 = mul2(v0, ff);
+                            v1 = mul2(v1, ff);
                         }
-                        // (h, l) += re0 (exact) + re1: TwoSum of the high word with the exact
+                        // (h, l) += v0 (exact) + v1: TwoSum of the high word with the exact
                         // leading part, then renormalise with the small terms so that the low
-                        // word never accumulates across groups
-                        float sh, se;
-                        two_sum(hre[j], re0, sh, se);
-                        two_sum(sh, (se + re1) + lre[j], hre[j], lre[j]);
-                        two_sum(him[j], im0, sh, se);
-                        two_sum(sh, (se + im1) + lim[j], him[j], lim[j]);
+                        // word never accumulates across groups (Re and Im in one packed pair)
+                        uint64_t sh, se;
+                        two_sum2(hw[j], v0, sh, se);
+                        two_sum2(sh, add2(add2(se, v1), lw[j]), hw[j], lw[j]);
                     }
                 }
                 fence_before();
@@ -535,9 +566,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const long long l = (long long)ti.J * (BM / 2) + 32 * half + 2 * j + cpar;
+                    float hre, him, lre, lim;
+                    upk2(hw[j], hre, him);
+                    upk2(lw[j], lre, lim);
                     if (l < n)
-                        Srow[l] = mk<double>(sc * ((double)hre[j] + (double)lre[j]),
-                                             sc * ((double)him[j] + (double)lim[j]));
+                        Srow[l] = mk<double>(sc * ((double)hre + (double)lre), sc * ((double)him + (double)lim));
                 }
             }
         }
