@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--eloc", default="diff32", choices=["diff32", "fp64"],
                     help="local energies: FP32 difference propagation (NQS_ELOC_DIFF32; its dtheta is checked "
                          "against the FP64 oracle in the same run) or the FP64-class arithmetic")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure FP64, FP32 (no TF32), TF32 and complex GEMM throughput with torch/cuBLAS and CUDA "
+                         "events (the denominators of the FP64 and FP32 stages)")
     ap.add_argument("--batch8x8", action="store_true",
                     help="the 16-instance batched 8x8 workload (12-layer FFNNs, N_s 2048-8192) through "
                          "sr_step_batched in instance groups that fit the memory budget")
@@ -711,6 +714,44 @@ def run_sharded(args, rank: int, world: int, local_rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_peaks(args) -> None:
+    """cuBLAS GEMM throughput by precision (best of 10 timed runs after warm-up, CUDA events)."""
+    import torch
+    out = {}
+
+    def timed(fn, flops, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            e.synchronize()
+            best = min(best, s.elapsed_time(e) / 1e3)
+        return flops / best / 1e12
+
+    n = 8192
+    for name, dt, tf32 in (("fp64", torch.float64, False), ("fp32", torch.float32, False),
+                           ("tf32", torch.float32, True), ("bf16", torch.bfloat16, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        out[name + "_tflops"] = timed(lambda: torch.matmul(a, b), 2.0 * n ** 3)
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    nc = 4096
+    a = torch.randn(nc, nc, dtype=torch.complex128, device="cuda")
+    b = torch.randn(nc, nc, dtype=torch.complex128, device="cuda")
+    out["c128_tflops"] = timed(lambda: torch.matmul(a, b), 8.0 * nc ** 3)
+    print(json.dumps({"peaks": out, "how": f"torch.matmul {n}^3 (real, 2 n^3 flops) and {nc}^3 complex128 "
+                      "(8 n^3 real flops), best of 10 after 3 warm-ups, CUDA events", "gpu": torch.cuda.get_device_name()}),
+          flush=True)
+
+
 def run_batch8x8(args) -> None:
     """All 16 instances of the batched 8x8 workload per step (one SR step of each), grouped by
     plan_batch_chunks so that one reused workspace of at most --batch-budget-gb fits."""
@@ -787,7 +828,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.batch8x8:
+    if args.peaks:
+        run_peaks(args)
+    elif args.batch8x8:
         run_batch8x8(args)
     elif args.sharded:
         run_sharded(args, rank, world, local_rank)

@@ -261,6 +261,19 @@ __global__ void __launch_bounds__(CP) chol_potrf_kernel(CBufs B, int k) {
     if (t == 0 && spiv) atomicOr(&B.flags[blockIdx.x], CF_PIVOT);
 }
 
+// Two-lane FP32 fused multiply-add (sm_100-class): (a0 b0 + c0, a1 b1 + c1), each rounded once.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long pk2f(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 // C (CT x CT) = C - A B^H (SUB) or C = A B^H, row-major tiles in global memory. Thread
 // (tx, ty) = (t % 16, t / 16) owns rows ty + 16 i and columns tx + 16 j (i, j < 4): the
 // rows read by a warp are two broadcasts, the columns sixteen consecutive padded rows.
@@ -274,26 +287,38 @@ __device__ __forceinline__ void tile_mul_nh(const c64* __restrict__ Ag, const c6
     }
     __syncthreads();
     const int tx = t & 15, ty = t >> 4;
+    // accumulators as packed (Re, Im) pairs: a conj(b) = (a.re, a.im) b.re + (a.im, -a.re) b.im,
+    // two two-lane FMAs per complex multiply-add
+    unsigned long long acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0ull;
+#pragma unroll 4
+    for (int l = 0; l < CT; ++l) {
+        unsigned long long a[4], as[4], br[4], bi[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const c64 v = As[(ty + 16 * i) * LDT + l];
+            a[i] = pk2f(v.re, v.im);
+            as[i] = pk2f(v.im, -v.re);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const c64 v = Bs[(tx + 16 * j) * LDT + l];
+            br[j] = pk2f(v.re, v.re);
+            bi[j] = pk2f(v.im, v.im);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = ffma2(as[i], bi[j], ffma2(a[i], br[j], acc[i][j]));
+    }
     float ar[4][4], ai[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0.f;
-#pragma unroll 4
-    for (int l = 0; l < CT; ++l) {
-        c64 a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[(ty + 16 * i) * LDT + l];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[(tx + 16 * j) * LDT + l];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {  // a conj(b)
-                ar[i][j] = fmaf(a[i].re, b[j].re, fmaf(a[i].im, b[j].im, ar[i][j]));
-                ai[i][j] = fmaf(a[i].im, b[j].re, fmaf(-a[i].re, b[j].im, ai[i][j]));
-            }
-    }
+        for (int j = 0; j < 4; ++j) asm("mov.b64 {%0, %1}, %2;" : "=f"(ar[i][j]), "=f"(ai[i][j]) : "l"(acc[i][j]));
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
