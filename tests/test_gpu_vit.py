@@ -143,3 +143,35 @@ def test_vit_vmc_trains_chain16(full_qgt):
     assert np.all(np.isfinite(out["energies"]))
     assert e_var >= e0 - 1e-9
     assert (e_var - e0) / abs(e0) < 5e-3, (e_var, e0)
+
+
+def test_vit_batched_with_rbm_equals_separate_steps():
+    """A transformer and an RBM instance in one sr_step_batched call (FP64) give the steps of
+    separate sr_step calls."""
+    ws = [W.make_workload("chain16_vit", 128), W.make_workload("chain10_rbm", 96)]
+    ins = [dev_inputs(w) for w in ws]
+    thetas = [ins[0][1] * 10, ins[1][1]]
+    dths, em, _, nk = nq().sr_step_batched([i[0] for i in ins], thetas, [i[2] for i in ins], [i[3] for i in ins],
+                                           [w.block_off for w in ws], 1e-2, 1e-10, 1.0, "fp64", solver="fp64")
+    for j, w in enumerate(ws):
+        model, _, x, ham = ins[j]
+        d1, e1, _, _ = nq().sr_step(model, thetas[j], x, ham, w.block_off, 1e-2, 1e-10, 1.0, "fp64", solver="fp64",
+                                    want_evals=False, param_space=True)
+        assert rel(dths[j].cpu().numpy(), d1.cpu().numpy()) < 1e-11, w.name
+        assert abs(em[j].item() - e1.cpu().numpy()[0]) <= 1e-12 * abs(e1.cpu().numpy()[0])
+
+
+def test_vit_sample_sharded_step_equals_unsharded():
+    """The transformer through the sample-sharded step (three shards simulated on one GPU:
+    shard sums, shard builds with the global means, owner solves) equals the one-call step."""
+    from paper_2510_08430_gb300 import sharded
+    w = W.make_workload("chain16_vit", 300)
+    model, theta, x, ham = dev_inputs(w)
+    theta = theta * 10
+    shards = [x[idx] for idx in np.array_split(np.arange(300), 3)]
+    be = sharded.LibraryShardBackend(model, ham, w.block_off, "fp64", "fp64")
+    dth, em = sharded.step_simulated(be, theta, shards, w.block_off, w.diag_shift, w.cutoff)
+    d1, e1, _, _ = nq().sr_step(model, theta, x, ham, w.block_off, w.diag_shift, w.cutoff, 1.0, "fp64", solver="fp64",
+                                want_evals=False, param_space=True)
+    assert rel(dth.cpu().numpy(), d1.cpu().numpy()) < 1e-11
+    assert abs(em.cpu().numpy()[0] - e1.cpu().numpy()[0]) <= 1e-12 * abs(e1.cpu().numpy()[0])
