@@ -355,7 +355,10 @@ NQS_API int qgt_block_build_shard(void* O, int64_t ldo, int64_t n_s, int64_t n_p
  *                  exceeds cutoff * upper bound (relative mode) or cutoff (absolute mode).
  *                  Certified blocks are then solved as the positive-definite system
  *                  S~_b x = F_b: FP32 tiled Cholesky of S~_b and FP64-residual iterative
- *                  refinement until ||F - S~ x|| <= 1e-14 ||F||; dtheta_b = -eta x equals the
+ *                  refinement until ||F - S~ x|| <= 1e-14 ||F|| (1e-12 ||F|| inside sr_step and
+ *                  sr_step_batched in the split precisions, whose S carries ~1e-10 relative
+ *                  error of its own), or until the residual stops contracting within 1e-12
+ *                  ||F||; dtheta_b = -eta x equals the
  *                  pseudo-inverse update up to rounding. A block that is not certified, meets
  *                  a non-positive FP32 pivot or does not converge sends every block to the
  *                  eigen-decomposition path above (one more host synchronisation); under

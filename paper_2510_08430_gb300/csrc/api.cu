@@ -125,6 +125,10 @@ inline bool eloc_dp(int prec, int flags) { return (flags & NQS_ELOC_DIFF32) && p
 inline int nsplit_of(int prec) {
     return prec == NQS_SPLIT_BF16 ? 2 : (prec == NQS_SPLIT_BF16X3 ? 3 : (prec == NQS_SPLIT_BF16_EXACT ? 5 : 0));
 }
+// Refinement target of the Cholesky solve inside a step: 1e-14 ||F||, or 1e-12 ||F|| when S comes
+// from a split Gram (whose own entry error is ~1e-10 relative); the solution error is then at
+// most 1e-12 kappa(S~) relative (1.4e-8 for kappa 1.4e4), far below the split's dtheta bar.
+inline double step_ref_tol(int prec) { return nsplit_of(prec) ? 1e-12 : 1e-14; }
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
 int check_prec(int prec) {
@@ -277,7 +281,7 @@ int run_build(void* O, long long ldo, long long ns, long long np, const double* 
 int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, double cutoff, int mode,
               double eta, int solver, c128* dtheta, double* evals, int32_t* n_kept, Arena& a, DevStatus* status,
               cudaStream_t st, cudaEvent_t trd_event = nullptr, cudaEvent_t trd_start = nullptr,
-              bool graph = false) {
+              bool graph = false, double ref_tol = 1e-14) {
     if (solver != NQS_SOLVE_FP64 && solver != NQS_SOLVE_MIXED && solver != NQS_SOLVE_MIXED_PSD)
         return fail(NQS_ERR_INVALID_ARG, "unknown solver %d", solver);
     if (!(shift >= 0.0)) return fail(NQS_ERR_INVALID_ARG, "diag_shift must be >= 0");
@@ -287,6 +291,7 @@ int run_solve(c128* S, const int64_t* off, int nb, const c128* F, double shift, 
     void* work = a.take(need);
     SolveArgs sa{shift, cutoff, eta, mode, evals != nullptr, solver != NQS_SOLVE_FP64, solver == NQS_SOLVE_MIXED_PSD,
                  trd_event, trd_start, graph, limits().ql_maxit};
+    sa.ref_tol = ref_tol;
     const int rc = launch_block_solve(S, off, nb, F, sa, dtheta, evals, n_kept, work, need, status, st);
     if (rc == NQS_ERR_UNSUPPORTED) return fail(rc, "block larger than the solver limit");
     if (rc != NQS_OK) return fail(rc, "block solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -533,7 +538,7 @@ int run_step_wide(const ModelDesc& md, const HamDesc& hd, const void* theta, con
         Arena sa2 = sa;
         rc = run_solve(w.S, wp.nar_off, wp.nnar, w.Fn, shift, cutoff, mode, eta,
                        solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver, w.dthn, nullptr, nk, sa2, status, st,
-                       nullptr, nullptr, graph);
+                       nullptr, nullptr, graph, step_ref_tol(prec));
         if (rc) return rc;
         for (int i = 0; i < wp.nnar; ++i) {
             const int b = wp.nar[i];
@@ -572,7 +577,7 @@ int run_step_wide(const ModelDesc& md, const HamDesc& hd, const void* theta, con
         CK(launch_ntk_rhs(w.e, ns, w.rhs, st), "rhs");
         Arena sa2 = sa;
         rc = run_solve(w.T, offT, 1, w.rhs, shift, cutoff, mode, -1.0, NQS_SOLVE_MIXED_PSD, w.u, nullptr, w.keptT, sa2,
-                       status, st, nullptr, nullptr, graph);
+                       status, st, nullptr, nullptr, graph, step_ref_tol(prec));
         if (rc) return rc;
         CK(launch_ntk_back(dOb, w.ldo, ns, n, w.u, eta, dtheta + off[b], st), "back-projection");
         if (n_kept) {
@@ -1210,7 +1215,7 @@ int sr_step(const nqs_model* m, const void* theta, const int8_t* configs, int64_
     const int sv = solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver;
     rc = run_solve(S, block_off, n_blocks, F, diag_shift, cutoff, cutoff_mode, eta, sv,
                    static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a, status, st, tm ? ws->ev[5] : nullptr,
-                   tm ? ws->ev[4] : nullptr, graph);
+                   tm ? ws->ev[4] : nullptr, graph, step_ref_tol(precision));
     if (rc) return rc;
     if (tm) {
         CK(cudaEventRecord(ws->ev[6], st), "event");
@@ -1444,7 +1449,8 @@ extern "C" int sr_step_batched(int32_t n_inst, const nqs_model* models, const vo
     if (!rc) {
         const int sv = solver == NQS_SOLVE_MIXED ? NQS_SOLVE_MIXED_PSD : solver;
         rc = run_solve(bb.S, bp->off_all, bp->nb_tot, bb.F, diag_shift, cutoff, cutoff_mode, eta, sv,
-                       static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a, status, st);
+                       static_cast<c128*>(dtheta_out), evals_out, n_kept_out, a, status, st, nullptr, nullptr, false,
+                       step_ref_tol(precision));
     }
     delete bp;
     delete tab;

@@ -30,7 +30,7 @@ constexpr int CTE = CT * CT;           // elements per tile
 constexpr int CP = 256;                // threads per CTA
 constexpr int LDT = CT + 1;            // padded leading dimension of shared tiles
 constexpr int CHOL_MAXT = 1024;        // tiles per block edge (n <= 65536)
-constexpr double CHOL_TOL = 1e-14;     // ||r|| <= CHOL_TOL ||F||, or
+constexpr double CHOL_TOL = 1e-14;     // default of ||r|| <= tol ||F|| (SolveArgs::ref_tol), or
 constexpr double CHOL_FLOOR = 1e-12;   // ||r|| <= CHOL_FLOOR ||F|| once ||r|| stops contracting (the
                                        // FP64 residual's rounding floor, ~n u ||S~|| ||x||)
 constexpr double PSD_MARGIN = 1e-6;    // rounding of a Gram matrix's eigenvalues, relative to ||S||
@@ -531,7 +531,7 @@ __device__ void residual_tile(const CBufs& B, const c128* __restrict__ S, const 
 __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128* __restrict__ S,
                                                              const c128* __restrict__ F, int nb, int Tmax,
                                                              double shift, int maxit, unsigned long long wait_ns,
-                                                             DevStatus* status) {
+                                                             double tol, DevStatus* status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     RefShared& sm = *reinterpret_cast<RefShared*>(smraw);
     const int t = threadIdx.x;
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(CP, 2) chol_refine_kernel(CBufs B, const c128*
                 if (!isfinite(s)) {
                     fin = true;
                     fl = CF_NONFINITE;
-                } else if (s <= CHOL_TOL * CHOL_TOL * fn) {
+                } else if (s <= tol * tol * fn) {
                     fin = true;
                 } else if (it >= 1 && s <= CHOL_FLOOR * CHOL_FLOOR * fn && s > 0.0625 * prev) {
                     fin = true;  // at the residual's rounding floor: no further sweep helps
@@ -1009,7 +1009,8 @@ int launch_chol_solve(const c128* S, const int64_t* block_off, int nb, const c12
         int nbv = nb, tm = Tmax, maxit = lim.ref_maxit;
         double shift = a.shift;
         unsigned long long wait_ns = lim.wait_ns;
-        void* args[] = {&B, (void*)&S, (void*)&F, &nbv, &tm, &shift, &maxit, &wait_ns, &status};
+        double tol = a.ref_tol > 0.0 ? a.ref_tol : CHOL_TOL;
+        void* args[] = {&B, (void*)&S, (void*)&F, &nbv, &tm, &shift, &maxit, &wait_ns, &tol, &status};
         count_launch();
         if (cudaLaunchCooperativeKernel((const void*)chol_refine_kernel, dim3(grid), dim3(CP), args, smem_ref, st) !=
             cudaSuccess)

@@ -204,6 +204,7 @@ struct SolveArgs {
     bool no_host_sync;          // capturable: the mixed certificate is checked on the device
     int ql_maxit;               // implicit-QL sweep limit per eigenvalue
     bool want_vectors;          // FP64 path: form every block's tridiagonal eigenvectors (QL)
+    double ref_tol = 1e-14;     // Cholesky path: refine until ||r|| <= ref_tol ||F|| (or the floor)
 };
 size_t solve_workspace_bytes(const int64_t* block_off, int nb);
 // Full FP64 eigen-decomposition of one n x n Hermitian matrix S (lower triangle used;
