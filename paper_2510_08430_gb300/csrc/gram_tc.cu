@@ -102,12 +102,6 @@ __device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t& s, ui
     e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
-// Error-free sum of two FP32 numbers: s + e = a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
