@@ -234,24 +234,33 @@ __global__ void __launch_bounds__(CP) chol_potrf_kernel(CBufs B, int k) {
         }
         __syncthreads();
     }
-    // inverse of the lower-triangular L: column c solves L x = e_c by forward substitution
-    if (t < CT) {
-        const int c = t;
-        for (int r = 0; r < c; ++r) X[r * LDT + c] = mk<float>(0.f, 0.f);
-        const c64 dc = A[c * LDT + c];
-        X[c * LDT + c] = mk<float>(1.f / dc.re, 0.f);
-        for (int r = c + 1; r < CT; ++r) {
-            float sr = 0.f, si = 0.f;
-            for (int l = c; l < r; ++l) {
-                const c64 a = A[r * LDT + l], xv = X[l * LDT + c];
-                sr += a.re * xv.re - a.im * xv.im;
-                si += a.re * xv.im + a.im * xv.re;
-            }
-            const float inv = 1.f / A[r * LDT + r].re;
-            X[r * LDT + c] = mk<float>(-sr * inv, -si * inv);
-        }
+    // inverse X = L^-1 of the lower-triangular L by right-looking substitution over the whole
+    // CTA: start from X = I; at step j row j of X is final once divided by L_jj, and every row
+    // r > j subtracts L_rj times it (columns <= j only)
+    for (int e = t; e < CT * CT; e += CP) {
+        const int r = e / CT, c = e - r * CT;
+        X[r * LDT + c] = mk<float>(r == c ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
+    for (int j = 0; j < CT; ++j) {
+        const float inv = 1.f / A[j * LDT + j].re;
+        if (t <= j) {
+            const c64 v = X[j * LDT + t];
+            X[j * LDT + t] = mk<float>(v.re * inv, v.im * inv);
+        }
+        __syncthreads();
+        // rows j+1 .. CT-1, columns 0 .. j: (CT - 1 - j) (j + 1) entries over the CTA
+        const int w = j + 1, nr = CT - 1 - j;
+        for (int e = t; e < nr * w; e += CP) {
+            const int r = j + 1 + e / w, c = e % w;
+            const c64 l = A[r * LDT + j], xj = X[j * LDT + c];
+            c64 v = X[r * LDT + c];
+            v.re -= l.re * xj.re - l.im * xj.im;
+            v.im -= l.re * xj.im + l.im * xj.re;
+            X[r * LDT + c] = v;
+        }
+        __syncthreads();
+    }
     c64* dinv = B.Dinv + (blk.doff + k) * CTE;
     for (int e = t; e < CTE; e += CP) {
         const int r = e / CT, c = e % CT;
